@@ -1,0 +1,58 @@
+"""Galerkin matrices by brute-force quadrature, and dense solves (oracle).
+
+Sec. 3.4.2 of the paper defines, with the discrete inner product of Eq. (quadrature),
+  mass        B_ml = (phi_l, phi_m)_w^N
+  stiffness   A_ml = (phi_l'', phi_m)_w^N
+and Sec. 4 (biharmonic problem) adds
+  bi-harmonic S_ml = (phi_l'''', phi_m)_w^N.
+Row index m is the test function, column index l the trial function.  Each entry
+is the quadrature sum over the N Chebyshev-Gauss points; nothing is taken from a
+closed form.
+
+For one Fourier column with squared wavenumber kappa2 (Eq. laplace), the weak
+forms of
+  a lap(u) + b u = f                       ->  (a (A - kappa2 B) + b B) u_hat = S(f)
+  a lap^2(u) + b lap(u) + c u = f          ->  (a (S - 2 kappa2 A + kappa2^2 B)
+                                                + b (A - kappa2 B) + c B) u_hat = S(f)
+after dividing both sides by the common Fourier factor (2 pi per periodic axis,
+or its domain length), are solved here by dense LU.
+"""
+import numpy as np
+
+from . import quadrature
+
+
+def matrices(kind, N):
+    """Dense B, A, S for the basis ``kind`` with N quadrature points."""
+    x, w = quadrature.gauss_points(N)
+    phi = quadrature.basis_values(kind, N, x, 0)          # (N, nb)
+    out = {}
+    for name, q in (("B", 0), ("A", 2), ("S", 4)):
+        dphi = quadrature.basis_values(kind, N, x, q)
+        out[name] = (phi * w[:, None]).T @ dphi             # [m, l] = sum_j phi_m(x_j) w_j phi_l^(q)(x_j)
+    return out
+
+
+def helmholtz_matrix(mats, a, b, kappa2):
+    return a * (mats["A"] - kappa2 * mats["B"]) + b * mats["B"]
+
+
+def biharmonic_matrix(mats, a, b, c, kappa2):
+    B, A, S = mats["B"], mats["A"], mats["S"]
+    return a * (S - 2.0 * kappa2 * A + kappa2 * kappa2 * B) + b * (A - kappa2 * B) + c * B
+
+
+def solve_columns(kind, N, rhs, kappa2, system):
+    """Solve system(kappa2) u = rhs along axis 0 for every column.
+
+    rhs has shape (N, ...) with the valid entries in rows 0..nb-1; kappa2 has
+    the shape of rhs[0].  Rows nb..N-1 of the result are zero.
+    """
+    nb = quadrature.num_basis(kind, N)
+    rhs = np.asarray(rhs)
+    cols = rhs.reshape(N, -1)
+    k2 = np.broadcast_to(kappa2, rhs.shape[1:]).reshape(-1)
+    out = np.zeros(cols.shape, dtype=np.result_type(cols.dtype, np.float64))
+    for c in range(cols.shape[1]):
+        out[:nb, c] = np.linalg.solve(system(k2[c]), cols[:nb, c])
+    return out.reshape(rhs.shape)

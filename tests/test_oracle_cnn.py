@@ -1,0 +1,49 @@
+"""Pins for the oracle's periodic 3x3 convolution network (CPU only)."""
+import numpy as np
+
+from oracle import closure_cnn as cnn
+
+
+def test_conv_forward_brute_force():
+    g = np.random.default_rng(2)
+    x = g.standard_normal((2, 5, 4))
+    W = g.standard_normal((3, 2, 3, 3))
+    b = g.standard_normal(3)
+    y = cnn.conv_forward(x, W, b)
+    C, H, Wd = x.shape
+    for o in range(3):
+        for i in range(H):
+            for j in range(Wd):
+                s = b[o]
+                for c in range(C):
+                    for p in range(3):
+                        for q in range(3):
+                            s += W[o, c, p, q] * x[c, (i + p - 1) % H, (j + q - 1) % Wd]
+                assert abs(y[o, i, j] - s) < 1e-12
+
+
+def test_network_gradients_finite_differences():
+    g = np.random.default_rng(3)
+    shapes = [(3, 2), (3, 3), (2, 3)]
+    params = [(g.standard_normal((o, c, 3, 3)) * 0.5, g.standard_normal(o) * 0.1) for o, c in shapes]
+    x = g.standard_normal((2, 5, 6))
+    gout = g.standard_normal((2, 5, 6))
+    out, acts = cnn.network_forward(x, params)
+    grads, gx = cnn.network_backward(params, acts, gout)
+    f = lambda ps, xx: np.sum(gout * cnn.network_forward(xx, ps)[0])
+    h = 1e-6
+    for li in range(len(params)):
+        for which in (0, 1):
+            arr = params[li][which]
+            for idx in [tuple(g.integers(0, s) for s in arr.shape) for _ in range(4)]:
+                old = arr[idx]
+                arr[idx] = old + h
+                fp = f(params, x)
+                arr[idx] = old - h
+                fm = f(params, x)
+                arr[idx] = old
+                assert abs((fp - fm) / (2 * h) - grads[li][which][idx]) < 1e-6
+    for idx in [(0, 1, 2), (1, 4, 5), (0, 0, 0)]:
+        xp = x.copy(); xp[idx] += h
+        xm = x.copy(); xm[idx] -= h
+        assert abs((f(params, xp) - f(params, xm)) / (2 * h) - gx[idx]) < 1e-6
