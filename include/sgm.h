@@ -1,0 +1,168 @@
+/*
+ * sgm.h - C ABI of libsgm, a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of the spectral Galerkin method of Mortensen, "Shenfun - automating the
+ * spectral Galerkin method" (arXiv 1708.03188).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every data pointer is a DEVICE pointer owned by the caller (for example a torch
+ *    tensor's data_ptr()), C-contiguous, and 16-byte aligned.  The library never frees
+ *    caller memory.  Objects created by the library (spaces, Ginzburg-Landau steppers)
+ *    own their device tables and workspaces and release them in the matching destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls are asynchronous on that stream; errors raised by a kernel after launch
+ *    are reported by a later call or by the caller's synchronisation.
+ *  - Every call returns an int status: SGM_OK (0) or a negative SGM_ERR_* code.
+ *    sgm_last_error() returns a thread-local message for the last failure.  Nothing
+ *    crosses the ABI as a C++ exception.
+ *  - Input and output arrays must not overlap (SGM_ERR_ALIAS), except where a call
+ *    says it works in place.
+ *
+ * Data layout (Sec. 4 of the paper; the default axis order of its TensorProductSpace)
+ * -------------------------------------------------------------------------------
+ *  A space has ndim axes.  Either axis 0 is a Chebyshev axis (SGM_CHEBYSHEV,
+ *  SGM_SHEN_DIRICHLET or SGM_SHEN_BIHARMONIC) and axes 1.. are Fourier axes, or all
+ *  axes are Fourier axes.  Only the last axis may be SGM_FOURIER_R2C.
+ *  Physical arrays have shape (n[0], ..., n[ndim-1]); they are real when the last
+ *  axis is R2C or the space is one Chebyshev axis alone, complex otherwise.
+ *  Spectral arrays are complex (interleaved re, im) of shape (n[0], ..., m) with
+ *  m = n[ndim-1]/2 + 1 for an R2C last axis, else n[ndim-1]; a 1-D Chebyshev
+ *  space has a real spectral array of length n[0].  Along the Chebyshev axis all n[0]
+ *  rows are stored; rows past the basis size (the index sets l^D = 0..N-3 of
+ *  Sec. 3.4.2 and l^B = 0..N-5 of Sec. 4) are written as zero.  Fourier axes are in
+ *  FFT order (l = 0, 1, ..., -2, -1).
+ *  Precision SGM_F32: float / complex64 arrays, FFTs and DCTs in FP32, every
+ *  Helmholtz, biharmonic and mass-matrix elimination in FP64 (inputs widened,
+ *  results rounded once).  SGM_F64: double / complex128 arrays, all arithmetic FP64.
+ *
+ * Normalisation (Sec. 3.4.1 and Sec. 3.4.2 of the paper)
+ * -----------------------------------------------------
+ *  Fourier forward:  u_hat_l = (1/M) sum_j u_j exp(-i l X_j), X_j = 2 pi j / M
+ *  Fourier backward: u_j = sum_l u_hat_l exp(i l X_j)
+ *  Shen scalar product on axis 0: S_k(u) = (u, phi_k)_w^N = (pi/N) sum_j u(x_j) phi_k(x_j),
+ *  x_j = cos((2j+1) pi / (2N)).  The 2 pi (or domain length) factors of the Fourier
+ *  inner products are divided out of both sides of every weak form.
+ */
+#ifndef SGM_H
+#define SGM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define SGM_OK 0
+#define SGM_ERR_NULL -1        /* a required pointer is NULL */
+#define SGM_ERR_SIZE -2        /* unsupported size, dimension or basis combination */
+#define SGM_ERR_ARG -3         /* invalid scalar argument */
+#define SGM_ERR_ALIAS -4       /* input and output overlap */
+#define SGM_ERR_ALIGN -5       /* pointer not 16-byte aligned */
+#define SGM_ERR_CUDA -6        /* a CUDA runtime call failed (message in sgm_last_error) */
+#define SGM_ERR_ALLOC -7       /* device or host allocation failed */
+#define SGM_ERR_STATE -8       /* object used after destroy or with a mismatched kind */
+
+/* basis kinds (Sec. 3.2 of the paper, the bases of shenfun.chebyshev and shenfun.fourier) */
+#define SGM_CHEBYSHEV 0          /* regular T_k, k = 0..N-1 */
+#define SGM_SHEN_DIRICHLET 1     /* T_k - T_{k+2}, k = 0..N-3 (Eq. chebdirichlet) */
+#define SGM_SHEN_BIHARMONIC 2    /* T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4}, k = 0..N-5 (Eq. chebbiharmonic) */
+#define SGM_FOURIER_C2C 3        /* exp(i l x), complex data */
+#define SGM_FOURIER_R2C 4        /* exp(i l x), real data, l = 0..M/2 stored (last axis only) */
+
+/* precision */
+#define SGM_F32 1                /* FP32 transforms, FP64 eliminations */
+#define SGM_F64 2                /* FP64 everywhere */
+
+/* shape selectors for sgm_space_shape */
+#define SGM_PHYSICAL 0
+#define SGM_SPECTRAL 1
+
+typedef struct sgm_space sgm_space;
+
+/* Thread-local description of the last failure on the calling thread. */
+const char* sgm_last_error(void);
+/* Static text for a status code. */
+const char* sgm_status_string(int status);
+
+/*
+ * Create a tensor-product space (the TensorProductSpace of Sec. 4; bases of Sec. 3.2).
+ *   out        receives the new space.
+ *   ndim       1..3.
+ *   kinds      ndim basis kinds (see above).
+ *   n          ndim sizes: quadrature points per axis (N >= 4 for Dirichlet, N >= 6 for
+ *              biharmonic; Fourier sizes >= 1).  Every size <= 4096.
+ *   domain     2*ndim doubles (lo, hi) per axis, or NULL for [-1,1] on a Chebyshev axis
+ *              and [0, 2 pi) on a Fourier axis.  A Fourier axis of length L = hi - lo is
+ *              mapped onto [0, 2 pi), so its derivatives scale by 2 pi / L (Sec. 6).
+ *              A Chebyshev axis must keep [-1, 1].
+ *   precision  SGM_F32 or SGM_F64.
+ * Allocates device tables and workspace on the current device (freed by destroy).
+ */
+int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n,
+                     const double* domain, int precision);
+/* Release a space and everything it owns.  NULL is accepted and ignored. */
+int sgm_space_destroy(sgm_space* space);
+/* Write the ndim extents of the PHYSICAL or SPECTRAL array into shape_out. */
+int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out);
+
+/*
+ * Scalar product S(F(f)) (the `inner(v, f)` of Sec. 3.4.2 and the right-hand side
+ * formula of Sec. 4): Fourier forward transforms (R2C on the last axis, then C2C axes
+ * from last to first), then the Shen scalar product on axis 0 computed as a DCT-II
+ * (via an FFT) with the basis stencil applied to the Chebyshev moments.
+ *   f        physical array;  f_tilde  spectral array (output).
+ * Pure Fourier spaces return the Fourier coefficients.
+ */
+int sgm_scalar_product(sgm_space* space, const void* f, void* f_tilde, void* stream);
+
+/*
+ * Forward transform u_hat = B^{-1} S(F(u)) (the projection T of Sec. 3.4.2): the scalar
+ * product followed by the mass-matrix solve along axis 0 in FP64.
+ */
+int sgm_forward(sgm_space* space, const void* u, void* u_hat, void* stream);
+
+/*
+ * Backward transform (Eq. fast_shen, then the inverse Fourier transforms): the basis
+ * stencil turns Shen coefficients into Chebyshev coefficients, a DCT-III (via an FFT)
+ * evaluates them at the Gauss points, then inverse C2C and C2R transforms.
+ */
+int sgm_backward(sgm_space* space, const void* u_hat, void* u, void* stream);
+
+/*
+ * Helmholtz/Poisson solve on a Shen-Dirichlet space (Eq. laplace; the Helmholtz solver of
+ * Sec. 4): for every Fourier column with squared wavenumber kappa^2 solve, in FP64,
+ *     (a (A - kappa^2 B) + b B) u_hat = f_tilde,
+ * the weak form of  a lap(u) + b u = f.  A is the stiffness matrix (phi_l'', phi_m)_w and
+ * B the mass matrix of Sec. 3.4.2.  Poisson -lap(u) = f is a = -1, b = 0.
+ *   f_tilde  spectral right-hand side (S(F(f)));  u_hat  spectral solution.
+ * Works in place (f_tilde == u_hat).  Requires axis 0 = SGM_SHEN_DIRICHLET.
+ * a = b = 0, or a system with a zero pivot, gives SGM_ERR_ARG / non-finite output.
+ */
+int sgm_helmholtz_solve(sgm_space* space, double a, double b, const void* f_tilde,
+                        void* u_hat, void* stream);
+
+/*
+ * Biharmonic solve on a Shen-biharmonic space (Sec. 4, the Biharmonic solver): for every
+ * Fourier column solve, in FP64,
+ *     (a (S - 2 kappa^2 A + kappa^4 B) + b (A - kappa^2 B) + c B) u_hat = f_tilde,
+ * the weak form of  a lap^2(u) + b lap(u) + c u = f,  S = (phi_l'''', phi_m)_w.
+ * The paper's problem lap^2(u) = f is a = 1, b = c = 0.  Works in place.
+ * Requires axis 0 = SGM_SHEN_BIHARMONIC.
+ */
+int sgm_biharmonic_solve(sgm_space* space, double a, double b, double c, const void* f_tilde,
+                         void* u_hat, void* stream);
+
+/*
+ * Physical-to-physical Helmholtz solve: u = backward(solve(scalar_product(f))), the whole
+ * pipeline of the paper's Fig. poisson2D in one call.  f and u are physical arrays.
+ */
+int sgm_helmholtz(sgm_space* space, double a, double b, const void* f, void* u, void* stream);
+/* Physical-to-physical biharmonic solve (scalar product, biharmonic solve, backward). */
+int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f, void* u,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGM_H */

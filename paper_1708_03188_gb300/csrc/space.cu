@@ -1,0 +1,569 @@
+// space.cu - host side of libsgm: the tensor-product space object, its device tables
+// (FFT twiddles, DCT twiddles, Galerkin coefficient tables), workspaces, and the C ABI
+// entry points declared in include/sgm.h.
+//
+// Pipelines (Sec. 4 of the paper, transform order: Fourier axes first on the way in):
+//   scalar product  rows(R2C|C2C fwd, last axis) -> strided C2C (middle axis, in place)
+//                   -> Chebyshev DCT-II + stencil (axis 0)
+//   forward         scalar product -> FP64 mass-matrix elimination (in place)
+//   backward        stencil + DCT-III (axis 0) -> strided inverse C2C -> rows (C2R|C2C inv)
+//   solve           FP64 elimination per Fourier column (k_solve.cu)
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sgm.h"
+#include "common.cuh"
+
+using namespace sgm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define SGM_CU(call)                                                                       \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess) return fail(SGM_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define SGM_TRY(expr)            \
+  do {                           \
+    int st_ = (expr);            \
+    if (st_ != SGM_OK) return st_; \
+  } while (0)
+
+const long double kPi = 3.141592653589793238462643383279502884L;
+
+FftPlan make_plan(int L) {
+  FftPlan p;
+  memset(&p, 0, sizeof p);
+  p.L = L;
+  int m = L;
+  auto push = [&](int r) { p.radix[p.npass++] = r; m /= r; };
+  while (m % 8 == 0 && p.npass < kMaxPasses) push(8);
+  if (m % 4 == 0) push(4);
+  if (m % 2 == 0) push(2);
+  while (m % 3 == 0) push(3);
+  while (m % 5 == 0) push(5);
+  for (int q = 7; m > 1; q += 2)
+    while (m % q == 0) push(q);
+  return p;
+}
+
+}  // namespace
+
+struct sgm_space {
+  static constexpr uint32_t kMagic = 0x5347'4d53u;
+  uint32_t magic = kMagic;
+  int device = 0;
+  int ndim = 0;
+  int kinds[3] = {0, 0, 0};
+  int64_t n[3] = {1, 1, 1};
+  double dom[6] = {0, 0, 0, 0, 0, 0};
+  int prec = SGM_F64;
+  bool cheb = false;       // axis 0 is a Chebyshev axis
+  bool real_phys = false;  // physical array is real
+  bool real_spec = false;  // spectral array is real (1-D Chebyshev)
+  int64_t spec[3] = {1, 1, 1};
+  long nphys = 0, nspec = 0;
+  size_t phys_bytes = 0, spec_bytes = 0;
+  std::map<int, void*> tw;   // length -> exp(-2 pi i k / L)
+  void* dctw = nullptr;      // exp(-i pi k / (2N))
+  double* tab = nullptr;     // Galerkin coefficient tables (Dirichlet or biharmonic)
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  double* scratch = nullptr;
+  long scratch_threads = 0;
+
+  size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
+  size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
+};
+
+namespace {
+
+template <typename T> int upload_twiddles(sgm_space* s, int L, void** out) {
+  std::vector<cplx<T>> h(L);
+  for (int k = 0; k < L; ++k) {
+    long double a = -2.0L * kPi * (long double)k / (long double)L;
+    h[k].x = (T)cosl(a);
+    h[k].y = (T)sinl(a);
+  }
+  SGM_CU(cudaMalloc(out, sizeof(cplx<T>) * L));
+  SGM_CU(cudaMemcpy(*out, h.data(), sizeof(cplx<T>) * L, cudaMemcpyHostToDevice));
+  return SGM_OK;
+}
+
+int need_tw(sgm_space* s, int L) {
+  if (s->tw.count(L)) return SGM_OK;
+  void* p = nullptr;
+  int st = s->prec == SGM_F32 ? upload_twiddles<float>(s, L, &p) : upload_twiddles<double>(s, L, &p);
+  if (st != SGM_OK) return st;
+  s->tw[L] = p;
+  return SGM_OK;
+}
+
+template <typename T> int upload_dctw(sgm_space* s, int N) {
+  std::vector<cplx<T>> h(N);
+  for (int k = 0; k < N; ++k) {
+    long double a = -kPi * (long double)k / (2.0L * N);
+    h[k].x = (T)cosl(a);
+    h[k].y = (T)sinl(a);
+  }
+  SGM_CU(cudaMalloc(&s->dctw, sizeof(cplx<T>) * N));
+  SGM_CU(cudaMemcpy(s->dctw, h.data(), sizeof(cplx<T>) * N, cudaMemcpyHostToDevice));
+  return SGM_OK;
+}
+
+// Galerkin coefficient tables, closed forms evaluated in long double.
+//   (T_a, T_b)_w = pi/2 c_a delta_ab;   (T_a'', T_b)_w = pi/2 a (a^2 - b^2), b < a, same parity;
+//   (T_a'''', T_b)_w = pi/2 a/24 [a^2 (a^2-4)^2 - 3 a^4 b^2 + 3 a^2 b^4 - b^2 (b^2-4)^2], b <= a-4.
+long double d2(int a, int b) {
+  if (b < a && ((a - b) & 1) == 0) return 0.5L * kPi * a * ((long double)a * a - (long double)b * b);
+  return 0.0L;
+}
+long double d4(int a, int b) {
+  if (b <= a - 4 && ((a - b) & 1) == 0) {
+    long double A = a, B = b;
+    long double P = A * A * (A * A - 4) * (A * A - 4) - 3 * A * A * A * A * B * B + 3 * A * A * B * B * B * B -
+                    B * B * (B * B - 4) * (B * B - 4);
+    return 0.5L * kPi * A / 24.0L * P;
+  }
+  return 0.0L;
+}
+struct Term { int idx; long double c; };
+void bih_terms(int k, Term t[3]) {
+  t[0] = {k, 1.0L};
+  t[1] = {k + 2, -2.0L * (k + 2) / (k + 3)};
+  t[2] = {k + 4, (long double)(k + 1) / (k + 3)};
+}
+
+int build_tables(sgm_space* s) {
+  const int N = (int)s->n[0];
+  const int ts = N + 8;
+  std::vector<double> h;
+  if (s->kinds[0] == SGM_SHEN_DIRICHLET) {
+    h.assign(3 * ts, 0.0);
+    for (int k = 0; k < N - 2; ++k) {
+      h[0 * ts + k] = (double)(0.5L * kPi * ((k == 0 ? 2 : 1) + 1));
+      h[1 * ts + k] = (double)(-2.0L * kPi * (k + 1) * (k + 2));
+      h[2 * ts + k] = (double)(-4.0L * kPi * (k + 1));
+    }
+  } else if (s->kinds[0] == SGM_SHEN_BIHARMONIC) {
+    enum { B0, B2, B4, ALO, A0, AUP, S0, S1, S2, G0, G1, F0, F1, COUNT };
+    h.assign(COUNT * ts, 0.0);
+    const int nb = N - 4;
+    auto pair = [&](int m, int l, long double (*f)(int, int)) {
+      Term tm[3], tl[3];
+      bih_terms(m, tm);
+      bih_terms(l, tl);
+      long double acc = 0;
+      for (auto& x : tl)
+        for (auto& y : tm) acc += x.c * y.c * f(x.idx, y.idx);
+      return acc;
+    };
+    for (int k = 0; k < nb; ++k) {
+      Term t[3];
+      bih_terms(k, t);
+      const long double ck = (k == 0) ? 2 : 1;
+      const long double be = t[1].c, ga = t[2].c;
+      const long double be2 = -2.0L * (k + 4) / (k + 5);
+      h[B0 * ts + k] = (double)(0.5L * kPi * (ck + be * be + ga * ga));
+      h[B2 * ts + k] = (double)(0.5L * kPi * (be + ga * be2));
+      h[B4 * ts + k] = (double)(0.5L * kPi * ga);
+      h[A0 * ts + k] = (double)pair(k, k, d2);
+      h[AUP * ts + k] = (double)pair(k, k + 2, d2);
+      h[ALO * ts + k] = k >= 2 ? (double)pair(k, k - 2, d2) : 0.0;
+      h[S0 * ts + k] = (double)pair(k, k, d4);
+      h[S1 * ts + k] = (double)pair(k, k + 2, d4);
+      h[S2 * ts + k] = (double)pair(k, k + 4, d4);
+      long double g0 = 0, g1 = 0, f0 = 0, f1 = 0;
+      for (auto& x : t) {
+        long double b2 = (long double)x.idx * x.idx;
+        g0 += x.c * b2 * b2;
+        g1 += x.c * b2 * b2 * b2;
+        f0 += x.c * x.idx / 24.0L * (3 * b2 + 8);
+        f1 += x.c * x.idx / 24.0L * (-1.0L);
+      }
+      h[G0 * ts + k] = (double)g0;
+      h[G1 * ts + k] = (double)g1;
+      h[F0 * ts + k] = (double)(0.5L * kPi * f0);
+      h[F1 * ts + k] = (double)(0.5L * kPi * f1);
+    }
+  } else {
+    return SGM_OK;
+  }
+  SGM_CU(cudaMalloc(&s->tab, sizeof(double) * h.size()));
+  SGM_CU(cudaMemcpy(s->tab, h.data(), sizeof(double) * h.size(), cudaMemcpyHostToDevice));
+  return SGM_OK;
+}
+
+int check_space(const sgm_space* s) {
+  if (!s) return fail(SGM_ERR_NULL, "space is NULL");
+  if (s->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != s->device)
+    return fail(SGM_ERR_STATE, "space was created on device %d, current device is %d", s->device, dev);
+  return SGM_OK;
+}
+
+int check_ptrs(const void* in, size_t in_bytes, const void* out, size_t out_bytes, bool allow_same) {
+  if (!in || !out) return fail(SGM_ERR_NULL, "NULL data pointer");
+  if (((uintptr_t)in & 15) || ((uintptr_t)out & 15)) return fail(SGM_ERR_ALIGN, "data pointers must be 16-byte aligned");
+  const char* a = (const char*)in;
+  const char* b = (const char*)out;
+  if (allow_same && a == b) return SGM_OK;
+  if (a < b + out_bytes && b < a + in_bytes) return fail(SGM_ERR_ALIAS, "input and output overlap");
+  return SGM_OK;
+}
+
+int wrap(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) return fail(SGM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  return SGM_OK;
+}
+
+int first_fourier(const sgm_space* s) { return s->cheb ? 1 : 0; }
+
+// Fourier forward on axes first_fourier..ndim-1: in (physical) -> out (complex).
+template <typename T> int fourier_forward(sgm_space* s, const void* in, void* out, cudaStream_t st) {
+  const int d = s->ndim - 1;
+  const int L = (int)s->n[d];
+  long nrows = 1;
+  for (int i = 0; i < d; ++i) nrows *= s->n[i];
+  const bool r2c = s->kinds[d] == SGM_FOURIER_R2C;
+  const int fl = (r2c && L % 2 == 0) ? L / 2 : L;
+  FftPlan p = make_plan(fl);
+  SGM_TRY(need_tw(s, fl));
+  SGM_TRY(need_tw(s, L));
+  SGM_TRY(wrap(launch_rows<T>(r2c ? kRowR2C : kRowC2CFwd, in, out, nrows, L, p, (const cplx<T>*)s->tw[fl],
+                              (const cplx<T>*)s->tw[L], st), "rows forward"));
+  for (int a = d - 1; a >= first_fourier(s); --a) {
+    long outer = 1, inner = 1;
+    for (int i = 0; i < a; ++i) outer *= s->spec[i];
+    for (int i = a + 1; i < s->ndim; ++i) inner *= s->spec[i];
+    const int La = (int)s->n[a];
+    FftPlan pa = make_plan(La);
+    SGM_TRY(need_tw(s, La));
+    SGM_TRY(wrap(launch_strided<T>(false, out, out, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
+                 "strided forward"));
+  }
+  return SGM_OK;
+}
+
+// Fourier backward: in (complex spectral-like) -> out (physical).  `in` is read only if
+// at most one Fourier axis exists, or copied through W1 otherwise (W1 may equal in).
+template <typename T> int fourier_backward(sgm_space* s, const void* in, void* out, cudaStream_t st) {
+  const int d = s->ndim - 1;
+  const void* cur = in;
+  for (int a = first_fourier(s); a < d; ++a) {
+    long outer = 1, inner = 1;
+    for (int i = 0; i < a; ++i) outer *= s->spec[i];
+    for (int i = a + 1; i < s->ndim; ++i) inner *= s->spec[i];
+    const int La = (int)s->n[a];
+    FftPlan pa = make_plan(La);
+    SGM_TRY(need_tw(s, La));
+    SGM_TRY(wrap(launch_strided<T>(true, cur, s->W1, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
+                 "strided backward"));
+    cur = s->W1;
+  }
+  const int L = (int)s->n[d];
+  long nrows = 1;
+  for (int i = 0; i < d; ++i) nrows *= s->n[i];
+  const bool r2c = s->kinds[d] == SGM_FOURIER_R2C;
+  const int fl = (r2c && L % 2 == 0) ? L / 2 : L;
+  FftPlan p = make_plan(fl);
+  SGM_TRY(need_tw(s, fl));
+  SGM_TRY(need_tw(s, L));
+  return wrap(launch_rows<T>(r2c ? kRowC2R : kRowC2CInv, cur, out, nrows, L, p, (const cplx<T>*)s->tw[fl],
+                             (const cplx<T>*)s->tw[L], st),
+              "rows backward");
+}
+
+template <typename T> int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st) {
+  const int N = (int)s->n[0];
+  long inner = 1;
+  for (int i = 1; i < s->ndim; ++i) inner *= s->spec[i];
+  FftPlan p = make_plan(N);
+  SGM_TRY(need_tw(s, N));
+  return wrap(launch_cheb<T>(mode, s->kinds[0], s->real_spec, in, out, N, inner, p, (const cplx<T>*)s->tw[N],
+                             (const cplx<T>*)s->dctw, st),
+              "chebyshev pass");
+}
+
+Wavenumbers wavenumbers(const sgm_space* s) {
+  Wavenumbers w;
+  memset(&w, 0, sizeof w);
+  w.n1 = w.n2 = 1;
+  w.m1 = w.m2 = 1;
+  auto scale = [&](int ax) {
+    double L = s->dom[2 * ax + 1] - s->dom[2 * ax];
+    double k = 2.0 * 3.14159265358979323846 / L;
+    return k * k;
+  };
+  if (s->ndim == 2) {
+    w.n2 = (int)s->spec[1];
+    w.m2 = (int)s->n[1];
+    w.r2c2 = s->kinds[1] == SGM_FOURIER_R2C;
+    w.s2 = scale(1);
+  } else if (s->ndim == 3) {
+    w.n1 = (int)s->spec[1];
+    w.m1 = (int)s->n[1];
+    w.r2c1 = 0;
+    w.s1 = scale(1);
+    w.n2 = (int)s->spec[2];
+    w.m2 = (int)s->n[2];
+    w.r2c2 = s->kinds[2] == SGM_FOURIER_R2C;
+    w.s2 = scale(2);
+  }
+  return w;
+}
+
+template <typename T>
+int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void* in, void* out, cudaStream_t st) {
+  long ncols = 1;
+  for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
+  return wrap(launch_solve<T>(basis, s->real_spec, a, b, c, in, out, (int)s->n[0], ncols, wavenumbers(s), s->tab,
+                              s->scratch, s->scratch_threads, st),
+              "solve");
+}
+
+template <typename T> int scalar_impl(sgm_space* s, const void* f, void* out, cudaStream_t st, int mode) {
+  if (!s->cheb) return fourier_forward<T>(s, f, out, st);
+  if (s->ndim == 1) return cheb_pass<T>(s, mode, f, out, st);
+  SGM_TRY(fourier_forward<T>(s, f, s->W1, st));
+  return cheb_pass<T>(s, mode, s->W1, out, st);
+}
+
+template <typename T> int forward_impl(sgm_space* s, const void* u, void* out, cudaStream_t st) {
+  if (!s->cheb) return fourier_forward<T>(s, u, out, st);
+  const int basis = s->kinds[0];
+  if (basis == SGM_CHEBYSHEV) return scalar_impl<T>(s, u, out, st, kChebForwardT);
+  SGM_TRY(scalar_impl<T>(s, u, out, st, kChebScalar));
+  if (basis == SGM_SHEN_DIRICHLET) return solve_impl<T>(s, kDirichlet, 0.0, 1.0, 0.0, out, out, st);
+  return solve_impl<T>(s, kBiharmonic, 0.0, 0.0, 1.0, out, out, st);
+}
+
+template <typename T> int backward_impl(sgm_space* s, const void* uh, void* u, cudaStream_t st) {
+  if (!s->cheb) {
+    if (s->ndim == 1) return fourier_backward<T>(s, uh, u, st);
+    return fourier_backward<T>(s, uh, u, st);
+  }
+  if (s->ndim == 1) return cheb_pass<T>(s, kChebBackward, uh, u, st);
+  SGM_TRY(cheb_pass<T>(s, kChebBackward, uh, s->W1, st));
+  return fourier_backward<T>(s, s->W1, u, st);
+}
+
+void free_space(sgm_space* s) {
+  for (auto& kv : s->tw) cudaFree(kv.second);
+  s->tw.clear();
+  cudaFree(s->dctw);
+  cudaFree(s->tab);
+  cudaFree(s->W1);
+  cudaFree(s->W2);
+  cudaFree(s->scratch);
+  s->magic = 0;
+  delete s;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sgm_last_error(void) { return g_err.c_str(); }
+
+const char* sgm_status_string(int status) {
+  switch (status) {
+    case SGM_OK: return "ok";
+    case SGM_ERR_NULL: return "NULL pointer";
+    case SGM_ERR_SIZE: return "unsupported size or basis combination";
+    case SGM_ERR_ARG: return "invalid argument";
+    case SGM_ERR_ALIAS: return "input and output overlap";
+    case SGM_ERR_ALIGN: return "misaligned pointer";
+    case SGM_ERR_CUDA: return "CUDA error";
+    case SGM_ERR_ALLOC: return "allocation failed";
+    case SGM_ERR_STATE: return "invalid object state";
+    default: return "unknown status";
+  }
+}
+
+int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n, const double* domain,
+                     int precision) {
+  if (!out || !kinds || !n) return fail(SGM_ERR_NULL, "out, kinds and n must be non-NULL");
+  *out = nullptr;
+  if (ndim < 1 || ndim > 3) return fail(SGM_ERR_SIZE, "ndim must be 1..3 (got %d)", ndim);
+  if (precision != SGM_F32 && precision != SGM_F64) return fail(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
+  const bool cheb = kinds[0] == SGM_CHEBYSHEV || kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC;
+  for (int d = 0; d < ndim; ++d) {
+    const int k = kinds[d];
+    if (k < SGM_CHEBYSHEV || k > SGM_FOURIER_R2C) return fail(SGM_ERR_ARG, "axis %d: unknown basis kind %d", d, k);
+    if (d > 0 && k <= SGM_SHEN_BIHARMONIC) return fail(SGM_ERR_SIZE, "axis %d: a Chebyshev basis must be axis 0", d);
+    if (k == SGM_FOURIER_R2C && d != ndim - 1) return fail(SGM_ERR_SIZE, "axis %d: only the last axis may be R2C", d);
+    if (n[d] < 1 || n[d] > 4096) return fail(SGM_ERR_SIZE, "axis %d: size %lld outside 1..4096", d, (long long)n[d]);
+  }
+  if (kinds[0] == SGM_SHEN_DIRICHLET && n[0] < 4) return fail(SGM_ERR_SIZE, "Dirichlet basis needs N >= 4");
+  if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "biharmonic basis needs N >= 6");
+  if (kinds[0] == SGM_CHEBYSHEV && n[0] < 2) return fail(SGM_ERR_SIZE, "Chebyshev basis needs N >= 2");
+  if (kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] < 2) return fail(SGM_ERR_SIZE, "R2C axis needs M >= 2");
+  if (cheb && domain && (domain[0] != -1.0 || domain[1] != 1.0))
+    return fail(SGM_ERR_ARG, "the Chebyshev axis domain must be [-1, 1]");
+  if (domain)
+    for (int d = 0; d < ndim; ++d)
+      if (!(domain[2 * d + 1] > domain[2 * d])) return fail(SGM_ERR_ARG, "axis %d: empty domain", d);
+
+  sgm_space* s = new (std::nothrow) sgm_space;
+  if (!s) return fail(SGM_ERR_ALLOC, "host allocation failed");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    delete s;
+    return fail(SGM_ERR_CUDA, "no CUDA device");
+  }
+  s->device = dev;
+  s->ndim = ndim;
+  s->prec = precision;
+  s->cheb = cheb;
+  for (int d = 0; d < ndim; ++d) {
+    s->kinds[d] = kinds[d];
+    s->n[d] = n[d];
+    s->spec[d] = n[d];
+    const bool cax = (d == 0 && cheb);
+    s->dom[2 * d] = domain ? domain[2 * d] : (cax ? -1.0 : 0.0);
+    s->dom[2 * d + 1] = domain ? domain[2 * d + 1] : (cax ? 1.0 : 2.0 * 3.14159265358979323846);
+  }
+  if (kinds[ndim - 1] == SGM_FOURIER_R2C) s->spec[ndim - 1] = n[ndim - 1] / 2 + 1;
+  s->real_phys = kinds[ndim - 1] == SGM_FOURIER_R2C || (cheb && ndim == 1);
+  s->real_spec = cheb && ndim == 1;
+  s->nphys = 1;
+  s->nspec = 1;
+  for (int d = 0; d < ndim; ++d) {
+    s->nphys *= n[d];
+    s->nspec *= s->spec[d];
+  }
+  s->phys_bytes = s->nphys * (s->real_phys ? s->relem() : s->celem());
+  s->spec_bytes = s->nspec * (s->real_spec ? s->relem() : s->celem());
+
+  int st = SGM_OK;
+  auto chk = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && st == SGM_OK) st = fail(SGM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+  };
+  const size_t wbytes = std::max(s->spec_bytes, (size_t)s->nspec * s->celem());
+  chk(cudaMalloc(&s->W1, wbytes), "workspace");
+  chk(cudaMalloc(&s->W2, wbytes), "workspace");
+  if (st == SGM_OK && cheb) {
+    const int N = (int)n[0];
+    st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);
+    if (st == SGM_OK) st = build_tables(s);
+    if (st == SGM_OK && (kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC)) {
+      int sms = 0;
+      chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
+      long ncols = s->nspec / N;
+      long need = 2 * ((ncols + 31) / 32) * 32;
+      need = ((need + 127) / 128) * 128;
+      s->scratch_threads = std::min((long)std::max(1, sms) * 256, need);
+      const long rows = N / 2 + 1;
+      const int nv = kinds[0] == SGM_SHEN_DIRICHLET ? 4 : 7;
+      chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
+    }
+  }
+  if (st != SGM_OK) {
+    free_space(s);
+    return st;
+  }
+  *out = s;
+  return SGM_OK;
+}
+
+int sgm_space_destroy(sgm_space* space) {
+  if (!space) return SGM_OK;
+  if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  free_space(space);
+  return SGM_OK;
+}
+
+int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out) {
+  if (!space || !shape_out) return fail(SGM_ERR_NULL, "NULL argument");
+  if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  if (which != SGM_PHYSICAL && which != SGM_SPECTRAL) return fail(SGM_ERR_ARG, "which must be PHYSICAL or SPECTRAL");
+  for (int d = 0; d < space->ndim; ++d) shape_out[d] = which == SGM_PHYSICAL ? space->n[d] : space->spec[d];
+  return SGM_OK;
+}
+
+int sgm_scalar_product(sgm_space* s, const void* f, void* f_tilde, void* stream) {
+  SGM_TRY(check_space(s));
+  SGM_TRY(check_ptrs(f, s->phys_bytes, f_tilde, s->spec_bytes, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->prec == SGM_F32 ? scalar_impl<float>(s, f, f_tilde, st, kChebScalar)
+                            : scalar_impl<double>(s, f, f_tilde, st, kChebScalar);
+}
+
+int sgm_forward(sgm_space* s, const void* u, void* u_hat, void* stream) {
+  SGM_TRY(check_space(s));
+  SGM_TRY(check_ptrs(u, s->phys_bytes, u_hat, s->spec_bytes, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->prec == SGM_F32 ? forward_impl<float>(s, u, u_hat, st) : forward_impl<double>(s, u, u_hat, st);
+}
+
+int sgm_backward(sgm_space* s, const void* u_hat, void* u, void* stream) {
+  SGM_TRY(check_space(s));
+  SGM_TRY(check_ptrs(u_hat, s->spec_bytes, u, s->phys_bytes, false));
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->prec == SGM_F32 ? backward_impl<float>(s, u_hat, u, st) : backward_impl<double>(s, u_hat, u, st);
+}
+
+static int solve_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u, void* stream) {
+  SGM_TRY(check_space(s));
+  if ((basis == kDirichlet && s->kinds[0] != SGM_SHEN_DIRICHLET) ||
+      (basis == kBiharmonic && s->kinds[0] != SGM_SHEN_BIHARMONIC))
+    return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
+  if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
+    return fail(SGM_ERR_ARG, "coefficients must be finite");
+  if (basis == kDirichlet && a == 0.0 && b == 0.0) return fail(SGM_ERR_ARG, "a = b = 0 gives a singular system");
+  if (basis == kBiharmonic && a == 0.0 && b == 0.0 && c == 0.0)
+    return fail(SGM_ERR_ARG, "a = b = c = 0 gives a singular system");
+  SGM_TRY(check_ptrs(f, s->spec_bytes, u, s->spec_bytes, true));
+  cudaStream_t st = (cudaStream_t)stream;
+  return s->prec == SGM_F32 ? solve_impl<float>(s, basis, a, b, c, f, u, st)
+                            : solve_impl<double>(s, basis, a, b, c, f, u, st);
+}
+
+int sgm_helmholtz_solve(sgm_space* s, double a, double b, const void* f_tilde, void* u_hat, void* stream) {
+  return solve_entry(s, kDirichlet, a, b, 0.0, f_tilde, u_hat, stream);
+}
+
+int sgm_biharmonic_solve(sgm_space* s, double a, double b, double c, const void* f_tilde, void* u_hat,
+                         void* stream) {
+  return solve_entry(s, kBiharmonic, a, b, c, f_tilde, u_hat, stream);
+}
+
+static int full_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u, void* stream) {
+  SGM_TRY(check_space(s));
+  SGM_TRY(check_ptrs(f, s->phys_bytes, u, s->phys_bytes, false));
+  SGM_TRY(sgm_scalar_product(s, f, s->W2, stream));
+  SGM_TRY(solve_entry(s, basis, a, b, c, s->W2, s->W2, stream));
+  return sgm_backward(s, s->W2, u, stream);
+}
+
+int sgm_helmholtz(sgm_space* s, double a, double b, const void* f, void* u, void* stream) {
+  return full_entry(s, kDirichlet, a, b, 0.0, f, u, stream);
+}
+
+int sgm_biharmonic(sgm_space* s, double a, double b, double c, const void* f, void* u, void* stream) {
+  return full_entry(s, kBiharmonic, a, b, c, f, u, stream);
+}
+
+}  // extern "C"

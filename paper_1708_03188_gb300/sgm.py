@@ -1,0 +1,165 @@
+"""ctypes binding of libsgm (include/sgm.h): argument marshalling only.
+
+Every computation runs in the CUDA kernels of libsgm.so; this module checks tensor
+shapes and dtypes, passes device pointers and the current CUDA stream, and turns
+status codes into exceptions.  There is no CPU fallback: if libsgm.so is missing the
+first call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsgm.so")
+
+KINDS = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2, "c2c": 3, "r2c": 4}
+PRECISION = {"f32": 1, "f64": 2}
+_VP = ctypes.c_void_p
+_D = ctypes.c_double
+
+_SIGNATURES = {
+    "sgm_last_error": (ctypes.c_char_p, []),
+    "sgm_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "sgm_space_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int]),
+    "sgm_space_destroy": (ctypes.c_int, [_VP]),
+    "sgm_space_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "sgm_scalar_product": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_helmholtz_solve": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
+    "sgm_biharmonic_solve": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
+    "sgm_helmholtz": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
+    "sgm_biharmonic": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
+}
+
+_lib = None
+
+
+class SgmError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"libsgm status {status}: {message}")
+        self.status = status
+
+
+def lib():
+    """Load libsgm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1708_03188_gb300.build.build()")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def check(status):
+    if status != 0:
+        raise SgmError(status, lib().sgm_last_error().decode())
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return _VP(s.cuda_stream)
+
+
+def _ptr(t):
+    return _VP(t.data_ptr())
+
+
+class Space:
+    """Tensor-product space (one Chebyshev axis 0 + Fourier axes, or Fourier axes only).
+
+    kinds: names from KINDS; sizes: quadrature points per axis; domain: [(lo, hi)] per
+    axis or None; precision "f32" (FP32 transforms, FP64 solves) or "f64".
+    """
+
+    def __init__(self, kinds, sizes, domain=None, precision="f32"):
+        self.kinds = tuple(kinds)
+        self.sizes = tuple(int(s) for s in sizes)
+        self.precision = precision
+        nd = len(self.kinds)
+        k = (ctypes.c_int * nd)(*[KINDS[x] for x in self.kinds])
+        n = (ctypes.c_int64 * nd)(*self.sizes)
+        dom = None
+        if domain is not None:
+            flat = [float(v) for pair in domain for v in pair]
+            dom = (_D * len(flat))(*flat)
+        self._h = _VP()
+        check(lib().sgm_space_create(ctypes.byref(self._h), nd, k, n, dom, PRECISION[precision]))
+        self.physical_shape = self._shape(0)
+        self.spectral_shape = self._shape(1)
+        cheb = self.kinds[0] in ("chebyshev", "dirichlet", "biharmonic")
+        self.real_physical = self.kinds[-1] == "r2c" or (cheb and nd == 1)
+        self.real_spectral = cheb and nd == 1
+        rdt = torch.float32 if precision == "f32" else torch.float64
+        cdt = torch.complex64 if precision == "f32" else torch.complex128
+        self.physical_dtype = rdt if self.real_physical else cdt
+        self.spectral_dtype = rdt if self.real_spectral else cdt
+
+    def _shape(self, which):
+        out = (ctypes.c_int64 * len(self.kinds))()
+        check(lib().sgm_space_shape(self._h, which, out))
+        return tuple(int(v) for v in out)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sgm_space_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- helpers -------------------------------------------------------------------------
+    def _check(self, t, shape, dtype, name):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {dtype} of shape {shape}, got {t.dtype} {tuple(t.shape)}")
+
+    def empty_physical(self, device="cuda"):
+        return torch.empty(self.physical_shape, dtype=self.physical_dtype, device=device)
+
+    def empty_spectral(self, device="cuda"):
+        return torch.empty(self.spectral_shape, dtype=self.spectral_dtype, device=device)
+
+    def _run(self, fn, src, src_spec, dst_spec, out, stream, *scalars):
+        self._check(src, self.spectral_shape if src_spec else self.physical_shape,
+                    self.spectral_dtype if src_spec else self.physical_dtype, "input")
+        if out is None:
+            out = self.empty_spectral(src.device) if dst_spec else self.empty_physical(src.device)
+        self._check(out, self.spectral_shape if dst_spec else self.physical_shape,
+                    self.spectral_dtype if dst_spec else self.physical_dtype, "output")
+        args = [self._h] + [_D(float(s)) for s in scalars] + [_ptr(src), _ptr(out), _stream(stream)]
+        check(fn(*args))
+        return out
+
+    # ---- the calls of include/sgm.h ----------------------------------------------------------
+    def scalar_product(self, f, out=None, stream=None):
+        return self._run(lib().sgm_scalar_product, f, False, True, out, stream)
+
+    def forward(self, u, out=None, stream=None):
+        return self._run(lib().sgm_forward, u, False, True, out, stream)
+
+    def backward(self, u_hat, out=None, stream=None):
+        return self._run(lib().sgm_backward, u_hat, True, False, out, stream)
+
+    def helmholtz_solve(self, a, b, f_tilde, out=None, stream=None):
+        return self._run(lib().sgm_helmholtz_solve, f_tilde, True, True, out, stream, a, b)
+
+    def biharmonic_solve(self, a, b, c, f_tilde, out=None, stream=None):
+        return self._run(lib().sgm_biharmonic_solve, f_tilde, True, True, out, stream, a, b, c)
+
+    def helmholtz(self, a, b, f, out=None, stream=None):
+        return self._run(lib().sgm_helmholtz, f, False, False, out, stream, a, b)
+
+    def biharmonic(self, a, b, c, f, out=None, stream=None):
+        return self._run(lib().sgm_biharmonic, f, False, False, out, stream, a, b, c)
