@@ -1,0 +1,391 @@
+"""Benchmark: transform + solve throughput on the 3-D Chebyshev x Fourier x Fourier box.
+
+Workload (one step): on the space Shen basis (N=256, axis 0) x Fourier C2C 256 x Fourier
+R2C 256 on [-1,1] x [0,2pi)^2, FP32 transforms and FP64 eliminations,
+  1. Poisson     -lap(u) = f  on the Dirichlet basis   (physical f -> physical u)
+  2. biharmonic  lap^2(u) = f on the biharmonic basis  (physical f -> physical u)
+with the manufactured f of u = (1-x^2)^2 sin(y) cos(2z).  Each solve is the paper's
+scalar product -> per-wavenumber solve -> backward pipeline (Sec. 4).  The metric is
+Gdof/s = grid points carried through a complete transform+solve per second
+(2 x 256^3 per step, summed over ranks).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own independent replica (no collective on the
+data path); the timed region is bracketed by barriers and the slowest rank's time is
+reported.  --impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N0 = N1 = N2 = 256
+KINDS_P = ["dirichlet", "c2c", "r2c"]
+KINDS_B = ["biharmonic", "c2c", "r2c"]
+DOF_PER_STEP = 2 * N0 * N1 * N2
+METRIC = "Gdof/s transform+solve (3-D Poisson + biharmonic, Cheb 256 x Fourier 256 x R2C 256)"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def manufactured(kinds):
+    from paper_1708_03188_gb300 import inputs
+    x, y, z = inputs.mesh(kinds, (N0, N1, N2))
+    shape = (N0, N1, N2)
+    if kinds[0] == "dirichlet":
+        f = inputs.box3d_f_poisson(x, y, z)
+    else:
+        f = inputs.box3d_f_biharmonic(x, y, z)
+    return np.broadcast_to(f, shape), np.broadcast_to(inputs.box3d_u(x, y, z), shape)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def hbm_peak():
+    d, src = peaks()
+    for k in ("hbm_gbs", "hbm_GBps", "hbm"):
+        if k in d:
+            try:
+                return float(d[k]), src
+            except (TypeError, ValueError):
+                pass
+    return 6800.0, "fallback"
+
+
+# FP64 operations (an FMA counts 2) per Chebyshev row per complex Fourier column in the
+# eliminations of k_solve.cu: Dirichlet 28, biharmonic 62 (assembly of the row from the
+# coefficient tables, elimination of the sub-diagonal entries with their right-hand
+# sides, one reciprocal counted as 1, back substitution with the running tail sums).
+FLOPS_PER_ROW = {"dirichlet": 28, "biharmonic": 62}
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world, rank, local = dist_env()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1708_03188_gb300 import build
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1708_03188_gb300.sgm import Space
+
+    prec = args.precision
+    sp_p = Space(KINDS_P, (N0, N1, N2), precision=prec)
+    sp_b = Space(KINDS_B, (N0, N1, N2), precision=prec)
+    fP, uP_exact = manufactured(KINDS_P)
+    fB, uB_exact = manufactured(KINDS_B)
+    dt = sp_p.physical_dtype
+    f_p = torch.from_numpy(np.ascontiguousarray(fP)).to(dt).cuda()
+    f_b = torch.from_numpy(np.ascontiguousarray(fB)).to(dt).cuda()
+    u_p = sp_p.empty_physical()
+    u_b = sp_b.empty_physical()
+    stream = torch.cuda.current_stream()
+
+    def step():
+        sp_p.helmholtz(-1.0, 0.0, f_p, out=u_p)
+        sp_b.biharmonic(1.0, 0.0, 0.0, f_b, out=u_b)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    err_p = float(torch.linalg.vector_norm((u_p.double().cpu() - torch.from_numpy(np.ascontiguousarray(uP_exact))))
+                  / np.linalg.norm(uP_exact))
+    err_b = float(torch.linalg.vector_norm((u_b.double().cpu() - torch.from_numpy(np.ascontiguousarray(uB_exact))))
+                  / np.linalg.norm(uB_exact))
+
+    # ---- per-call breakdown (same stream, CUDA events, averaged) --------------------------------
+    def time_call(fn, reps):
+        for _ in range(2):
+            fn()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    reps = max(3, min(args.steps, 10))
+    sp_work = sp_p.empty_spectral()
+    sb_work = sp_b.empty_spectral()
+    sp_rhs = sp_p.scalar_product(f_p)
+    sb_rhs = sp_b.scalar_product(f_b)
+    br = {
+        "poisson_scalar_product_ms": time_call(lambda: sp_p.scalar_product(f_p, out=sp_work), reps),
+        "poisson_solve_ms": time_call(lambda: sp_p.helmholtz_solve(-1.0, 0.0, sp_rhs, out=sp_work), reps),
+        "poisson_backward_ms": time_call(lambda: sp_p.backward(sp_rhs, out=u_p), reps),
+        "biharmonic_scalar_product_ms": time_call(lambda: sp_b.scalar_product(f_b, out=sb_work), reps),
+        "biharmonic_solve_ms": time_call(lambda: sp_b.biharmonic_solve(1.0, 0.0, 0.0, sb_rhs, out=sb_work), reps),
+        "biharmonic_backward_ms": time_call(lambda: sp_b.backward(sb_rhs, out=u_b), reps),
+    }
+    ncols = N1 * (N2 // 2 + 1)
+    fl_b = FLOPS_PER_ROW["biharmonic"] * (N0 - 4) * ncols
+    fl_p = FLOPS_PER_ROW["dirichlet"] * (N0 - 2) * ncols
+    t_b = br["biharmonic_solve_ms"] * 1e-3
+    achieved = fl_b / t_b / 1e12
+    roofline = {"kernel": "k_solve_biharmonic (FP64 elimination, 33024 columns x 252 rows)",
+                "bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA probe measured 1.19)",
+                "dirichlet_solve_tflops": round(fl_p / (br["poisson_solve_ms"] * 1e-3) / 1e12, 4)}
+
+    # ---- end to end through host buffers (pinned), same step -----------------------------------
+    hf_p = torch.from_numpy(np.ascontiguousarray(fP)).to(dt).pin_memory()
+    hf_b = torch.from_numpy(np.ascontiguousarray(fB)).to(dt).pin_memory()
+    hu_p = torch.empty_like(hf_p).pin_memory()
+    hu_b = torch.empty_like(hf_b).pin_memory()
+
+    def e2e_step():
+        f_p.copy_(hf_p, non_blocking=True)
+        f_b.copy_(hf_b, non_blocking=True)
+        step()
+        hu_p.copy_(u_p, non_blocking=True)
+        hu_b.copy_(u_b, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    b.synchronize()
+    e2e_ms = a.elapsed_time(b) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    value = world * DOF_PER_STEP / (ms * 1e-3) / 1e9
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline() if world == 1 else None
+        ebytes = hf_p.element_size()
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gdof/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 transforms + f64 eliminations" if prec == "f32" else "f64",
+            "data": "synthetic (manufactured u=(1-x^2)^2 sin y cos 2z)",
+            "config": {"workload": "box3d 256^3: Poisson (Shen-Dirichlet) + biharmonic (Shen-biharmonic) x "
+                                   "Fourier C2C 256 x R2C 256, physical f -> physical u",
+                       "global_batch": world, "dof_per_step": DOF_PER_STEP, "parallelism": f"replicas x{world}",
+                       "l2": "working set > L2 (two 64 MiB inputs, two 64 MiB outputs, 4 x 64.5 MiB workspaces)"},
+            "error_vs_exact": {"poisson": err_p, "biharmonic": err_b},
+            "breakdown_ms": {k: round(v, 4) for k, v in br.items()},
+            "roofline": roofline,
+            "e2e": {"value": round(world * DOF_PER_STEP / (e2e_ms * 1e-3) / 1e9, 4), "unit": "Gdof/s",
+                    "h2d_bytes_per_step": 2 * N0 * N1 * N2 * ebytes, "d2h_bytes_per_step": 2 * N0 * N1 * N2 * ebytes,
+                    "ms_per_step": round(e2e_ms, 4)},
+            "gpu_launches": 14 * args.steps,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return line
+
+
+# ---- FP64 CPU oracle on a bounded sample of the same workload ---------------------------------------
+def oracle_step_sample(ncols_sample=1024, seed=0):
+    """One oracle pass over the Poisson half of the step, solves on a column sample.
+
+    Dense Fourier and Shen transforms on the full 256^3 box (as the oracle stands), dense LU
+    solves on `ncols_sample` of the 33024 Fourier columns, backward on the full box.
+    Returns (seconds measured, seconds extrapolated to the full Poisson solve).
+    """
+    from oracle import galerkin
+    from oracle.space import Space as OSpace
+    fP, _ = manufactured(KINDS_P)
+    sp = OSpace(KINDS_P, (N0, N1, N2))
+    t0 = time.perf_counter()
+    s = sp.scalar_product(np.ascontiguousarray(fP))
+    t1 = time.perf_counter()
+    mats = sp.matrices()
+    k2 = sp.kappa2().ravel()
+    cols = s.reshape(N0, -1)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(cols.shape[1], size=ncols_sample, replace=False)
+    uh = np.zeros_like(cols)
+    sub = galerkin.solve_columns("dirichlet", N0, cols[:, pick], k2[pick],
+                                 lambda v: galerkin.helmholtz_matrix(mats, -1.0, 0.0, v))
+    uh[:, pick] = sub
+    t2 = time.perf_counter()
+    sp.backward(uh.reshape(s.shape))
+    t3 = time.perf_counter()
+    full = (t1 - t0) + (t2 - t1) * cols.shape[1] / ncols_sample + (t3 - t2)
+    return t3 - t0, full
+
+
+def cpu_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("num_threads")]
+        if n:
+            return int(max(n))
+    except Exception:
+        pass
+    return os.cpu_count() or 1
+
+
+def cpu_baseline():
+    measured, poisson_full = oracle_step_sample()
+    # the biharmonic half costs the same dense transforms and a dense LU of the same size
+    step_s = 2 * poisson_full
+    return {"value": round(DOF_PER_STEP / step_s / 1e9, 8), "unit": "Gdof/s", "cores": cpu_threads(),
+            "kind": "oracle",
+            "sample": f"dense-DFT/dense-quadrature transforms of the full 256^3 Poisson box, dense LU on 1024 of "
+                      f"33024 columns scaled to all columns, doubled for the biharmonic half ({measured:.1f} s measured)"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        _, poisson_full = oracle_step_sample(ncols_sample=256, seed=i)
+        if i >= args.warmup:
+            times.append(2 * poisson_full)
+    step_s = float(np.mean(times))
+    value = DOF_PER_STEP / step_s / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "Gdof/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(step_s * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (manufactured u=(1-x^2)^2 sin y cos 2z)",
+            "config": {"workload": "box3d 256^3: Poisson + biharmonic, physical f -> physical u",
+                       "global_batch": 1, "dof_per_step": DOF_PER_STEP, "parallelism": "cpu"},
+            "cpu_baseline": {"value": round(value, 8), "unit": "Gdof/s", "cores": cpu_threads(), "kind": "oracle",
+                             "sample": "per step: dense transforms of the full Poisson box, dense LU on 256 of "
+                                       "33024 columns scaled to all columns, doubled for the biharmonic half"},
+            "e2e": {"value": round(value, 8), "unit": "Gdof/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return line
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
