@@ -162,6 +162,30 @@ int sgm_helmholtz(sgm_space* space, double a, double b, const void* f, void* u, 
 int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f, void* u,
                    void* stream);
 
+/*
+ * Dirichlet Helmholtz solve that allocates nothing (no counterpart in the paper; it is an
+ * interface choice of this library).
+ *
+ * For callers that must not allocate device memory themselves: programs whose device
+ * memory belongs to one memory manager (a framework's caching allocator, or a fixed budget
+ * reserved up front) and latency-critical loops that cannot afford the time or the possible
+ * failure of cudaMalloc.  sgm_space_create allocates, so those callers cannot use the space
+ * API; this entry point computes the same result as sgm_helmholtz_solve on a space built
+ * from the same arguments, with no space object and no cudaMalloc/cudaFree.
+ *   ndim, kinds, n, domain, precision   as for sgm_space_create; kinds[0] must be
+ *                                       SGM_SHEN_DIRICHLET and 4 <= n[0] <= 2048.
+ *   a, b, f_tilde, u_hat, stream        as for sgm_helmholtz_solve (in place allowed).
+ * Scratch: an 8 MiB array in the library's device memory, reserved on every GPU that loads
+ * the library and held until the process exits.  The first call on each device looks up
+ * the array's device address (with that device current); make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents
+ * (nothing in it needs to start at zero); calls whose kernels overlap on the GPU, e.g. on
+ * two streams, race on it, so serialise them.  Sizes past the limit return SGM_ERR_SIZE.
+ */
+int sgm_helmholtz_solve_noalloc(int ndim, const int* kinds, const int64_t* n, const double* domain,
+                                int precision, double a, double b, const void* f_tilde, void* u_hat,
+                                void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -67,6 +67,9 @@ __device__ __forceinline__ double kappa2_of(const Wavenumbers& w, long c) {
   return w.s1 * l1 * l1 + w.s2 * l2 * l2;
 }
 
+// ---- error reporting (space.cu): sets the thread-local message of sgm_last_error ---------
+int set_error(int code, const char* fmt, ...);
+
 // ---- launchers (defined in k_fourier.cu, k_cheb.cu, k_solve.cu) --------------------------
 // All return cudaGetLastError() after the launch.
 enum RowMode { kRowR2C = 0, kRowC2R = 1, kRowC2CFwd = 2, kRowC2CInv = 3 };

@@ -69,6 +69,16 @@ FftPlan make_plan(int L) {
 
 }  // namespace
 
+int sgm::set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
 struct sgm_space {
   static constexpr uint32_t kMagic = 0x5347'4d53u;
   uint32_t magic = kMagic;

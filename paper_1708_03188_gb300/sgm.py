@@ -32,6 +32,9 @@ _SIGNATURES = {
     "sgm_biharmonic_solve": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
     "sgm_helmholtz": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
     "sgm_biharmonic": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
+    "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                                   ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int,
+                                                   _D, _D, _VP, _VP, _VP]),
 }
 
 _lib = None
