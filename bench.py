@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    p.add_argument("--kernel", default=None,
+                   choices=["helmholtz_solve", "biharmonic_solve", "scalar_product", "backward", "step"],
+                   help="run only this call (warmup + steps times) for profiling; prints no bench line")
     return p.parse_args()
 
 
@@ -175,6 +178,20 @@ def run_ours(args):
         sp_p.helmholtz(-1.0, 0.0, f_p, out=u_p)
         sp_b.biharmonic(1.0, 0.0, 0.0, f_b, out=u_b)
 
+    if args.kernel is not None:
+        rhs_p, rhs_b = sp_p.scalar_product(f_p), sp_b.scalar_product(f_b)
+        work = sp_b.empty_spectral()
+        calls = {"helmholtz_solve": lambda: sp_p.helmholtz_solve(-1.0, 0.0, rhs_p, out=work),
+                 "biharmonic_solve": lambda: sp_b.biharmonic_solve(1.0, 0.0, 0.0, rhs_b, out=work),
+                 "scalar_product": lambda: sp_b.scalar_product(f_b, out=work),
+                 "backward": lambda: sp_b.backward(rhs_b, out=u_b),
+                 "step": step}
+        for _ in range(args.warmup + args.steps):
+            calls[args.kernel]()
+        torch.cuda.synchronize()
+        print(f"ran {args.kernel} x{args.warmup + args.steps}", flush=True)
+        return None
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -221,24 +238,36 @@ def run_ours(args):
     sb_work = sp_b.empty_spectral()
     sp_rhs = sp_p.scalar_product(f_p)
     sb_rhs = sp_b.scalar_product(f_b)
+    # the fused step keeps its spectral intermediate in FP64, so its eliminations are the
+    # FP64-data kernels: time them through f64 spaces of the same shape (same kernel, same
+    # launch configuration) on complex128 right-hand sides
+    sp_p64 = Space(KINDS_P, (N0, N1, N2), precision="f64")
+    sp_b64 = Space(KINDS_B, (N0, N1, N2), precision="f64")
+    rp64, rb64 = sp_rhs.to(torch.complex128), sb_rhs.to(torch.complex128)
+    wp64, wb64 = torch.empty_like(rp64), torch.empty_like(rb64)
     br = {
+        "poisson_step_ms": time_call(lambda: sp_p.helmholtz(-1.0, 0.0, f_p, out=u_p), reps),
+        "poisson_solve_kernel_ms": time_call(lambda: sp_p64.helmholtz_solve(-1.0, 0.0, rp64, out=wp64), reps),
         "poisson_scalar_product_ms": time_call(lambda: sp_p.scalar_product(f_p, out=sp_work), reps),
-        "poisson_solve_ms": time_call(lambda: sp_p.helmholtz_solve(-1.0, 0.0, sp_rhs, out=sp_work), reps),
         "poisson_backward_ms": time_call(lambda: sp_p.backward(sp_rhs, out=u_p), reps),
+        "biharmonic_step_ms": time_call(lambda: sp_b.biharmonic(1.0, 0.0, 0.0, f_b, out=u_b), reps),
+        "biharmonic_solve_kernel_ms": time_call(lambda: sp_b64.biharmonic_solve(1.0, 0.0, 0.0, rb64, out=wb64), reps),
         "biharmonic_scalar_product_ms": time_call(lambda: sp_b.scalar_product(f_b, out=sb_work), reps),
-        "biharmonic_solve_ms": time_call(lambda: sp_b.biharmonic_solve(1.0, 0.0, 0.0, sb_rhs, out=sb_work), reps),
         "biharmonic_backward_ms": time_call(lambda: sp_b.backward(sb_rhs, out=u_b), reps),
     }
+    sp_p64.close()
+    sp_b64.close()
+    del rp64, rb64, wp64, wb64
     ncols = N1 * (N2 // 2 + 1)
     fl_b = FLOPS_PER_ROW["biharmonic"] * (N0 - 4) * ncols
     fl_p = FLOPS_PER_ROW["dirichlet"] * (N0 - 2) * ncols
-    t_b = br["biharmonic_solve_ms"] * 1e-3
+    t_b = br["biharmonic_solve_kernel_ms"] * 1e-3
     achieved = fl_b / t_b / 1e12
-    roofline = {"kernel": "k_solve_biharmonic (FP64 elimination, 33024 columns x 252 rows)",
+    roofline = {"kernel": "k_solve_biharmonic<double,2> (FP64 elimination, 33024 columns x 252 rows)",
                 "bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
                 "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA probe measured 1.19)",
-                "dirichlet_solve_tflops": round(fl_p / (br["poisson_solve_ms"] * 1e-3) / 1e12, 4)}
+                "dirichlet_solve_tflops": round(fl_p / (br["poisson_solve_kernel_ms"] * 1e-3) / 1e12, 4)}
 
     # ---- end to end through host buffers (pinned), same step -----------------------------------
     hf_p = torch.from_numpy(np.ascontiguousarray(fP)).to(dt).pin_memory()

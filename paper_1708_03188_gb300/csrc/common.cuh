@@ -85,7 +85,22 @@ cudaError_t launch_strided(bool inverse, const void* in, void* out, long outer, 
 enum ChebMode { kChebScalar = 0, kChebBackward = 1, kChebForwardT = 2 };
 template <typename T>
 cudaError_t launch_cheb(int mode, int basis, bool real, const void* in, void* out, int N, long inner,
-                        const FftPlan& plan, const cplx<T>* tw, const cplx<T>* dctw, cudaStream_t s);
+                        const FftPlan& plan, const cplx<T>* tw, const cplx<T>* dctw, cudaStream_t s,
+                        bool wide = false);
+
+// FP64 values per Chebyshev row per thread in the elimination scratch (k_solve.cu).
+int solve_scratch_values(int basis);
+// compile-time-length transforms (k_fast_*.cu), for lengths with fast_compiled(L)
+bool fast_compiled(int L);
+template <typename T>
+cudaError_t launch_rows_fast(int mode, const void* in, void* out, long nrows, int L, const cplx<T>* twf,
+                             const cplx<T>* tw_L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_strided_fast(bool inverse, const void* in, void* out, long outer, int L, long inner,
+                                const cplx<T>* twf, cudaStream_t s);
+template <typename T>
+cudaError_t launch_cheb_fast(int mode, int basis, bool real, const void* in, void* out, int N, long inner,
+                             const cplx<T>* twf, const cplx<T>* dctw, cudaStream_t s, bool wide);
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out,

@@ -22,8 +22,13 @@
 // A CTA stages TW neighbouring columns (contiguous in memory) of all N rows, so the
 // global reads and writes are whole 128-byte lines, and transforms them as TW lines
 // in shared memory.  `real` = a real 1-D column (imaginary parts zero / dropped).
+// TS is the storage type of the spectral-side array: T, or double while computing in
+// FP32 (the physical-to-physical solves keep their spectral intermediate in FP64 so the
+// FP64 eliminations read and write it without conversions; the conversions happen here
+// on the integer pipe, convert.cuh).
 #include <algorithm>
 
+#include "convert.cuh"
 #include "fft_core.cuh"
 
 namespace sgm {
@@ -35,7 +40,7 @@ __device__ __forceinline__ int nbasis(int basis, int N) {
   return basis == kDirichlet ? N - 2 : (basis == kBiharmonic ? N - 4 : N);
 }
 
-template <typename T, int MODE>
+template <typename T, int MODE, typename TS>
 __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void* __restrict__ out, int N, long inner,
                                               int basis, int real, const __grid_constant__ FftPlan plan,
                                               const cplx<T>* __restrict__ tw, const cplx<T>* __restrict__ dctw,
@@ -51,6 +56,7 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
   const C* src = reinterpret_cast<const C*>(in);
   const T* srcr = reinterpret_cast<const T*>(in);
 
+  // physical side (input of the scalar product, output of the backward transform): type T
   auto load = [&](int i, int t) -> C {
     const long g = (long)i * inner + t0 + t;
     return real ? mk<C>(srcr[g], (T)0) : src[g];
@@ -59,6 +65,13 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
     const long g = (long)i * inner + t0 + t;
     if (real) reinterpret_cast<T*>(out)[g] = v.x;
     else reinterpret_cast<C*>(out)[g] = v;
+  };
+  // spectral side: type TS
+  auto load_spec = [&](int i, int t) -> C {
+    return from_spec<TS, C>(reinterpret_cast<const TS*>(in), (long)i * inner + t0 + t, real);
+  };
+  auto store_spec = [&](int i, int t, C v) {
+    to_spec<TS, C>(reinterpret_cast<TS*>(out), (long)i * inner + t0 + t, real, v);
   };
 
   if (MODE == kChebScalar || MODE == kChebForwardT) {
@@ -99,12 +112,12 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
           s = mk<C>(m[k].x + be * m[k + 2].x + ga * m[k + 4].x, m[k].y + be * m[k + 2].y + ga * m[k + 4].y);
         }
       }
-      store(k, t, s);
+      store_spec(k, t, s);
     }
   } else {  // backward
     for (int idx = threadIdx.x; idx < N * TW; idx += blockDim.x) {
       const int k = idx / TW, t = idx - k * TW;
-      if (t < nt) B[t * ld + k] = (k < nb) ? load(k, t) : mk<C>((T)0, (T)0);
+      if (t < nt) B[t * ld + k] = (k < nb) ? load_spec(k, t) : mk<C>((T)0, (T)0);
     }
     __syncthreads();
     // stencil: Shen -> Chebyshev coefficients, into A
@@ -146,34 +159,35 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
 
 template <typename T>
 cudaError_t launch_cheb(int mode, int basis, bool real, const void* in, void* out, int N, long inner,
-                        const FftPlan& plan, const cplx<T>* tw, const cplx<T>* dctw, cudaStream_t s) {
+                        const FftPlan& plan, const cplx<T>* tw, const cplx<T>* dctw, cudaStream_t s, bool wide) {
   if (inner <= 0) return cudaSuccess;
   const int TWmax = real ? 1 : (sizeof(T) == 4 ? 16 : 8);
   const int TW = (int)std::max(1L, std::min((long)TWmax, (long)(kSmemBudget / (2 * sizeof(cplx<T>) * (N + 1)))));
   const size_t smem = 2 * sizeof(cplx<T>) * (size_t)TW * (N + 1);
   const unsigned grid = (unsigned)((inner + TW - 1) / TW);
   cudaError_t e = cudaSuccess;
+  auto go = [&](auto kernel) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (err != cudaSuccess) return err;
+    }
+    kernel<<<grid, 256, smem, s>>>(in, out, N, inner, basis, real ? 1 : 0, plan, tw, dctw, TW);
+    return cudaSuccess;
+  };
+  const bool w = wide && sizeof(T) == 4;
   switch (mode) {
-#define SGM_CHEB(M)                                                                                 \
-  case M:                                                                                           \
-    if (smem > 48 * 1024 &&                                                                         \
-        (e = cudaFuncSetAttribute(k_cheb<T, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != \
-            cudaSuccess)                                                                            \
-      return e;                                                                                     \
-    k_cheb<T, M><<<grid, 256, smem, s>>>(in, out, N, inner, basis, real ? 1 : 0, plan, tw, dctw, TW);  \
-    break;
-    SGM_CHEB(kChebScalar)
-    SGM_CHEB(kChebBackward)
-    SGM_CHEB(kChebForwardT)
-#undef SGM_CHEB
+    case kChebScalar: e = w ? go(k_cheb<T, kChebScalar, double>) : go(k_cheb<T, kChebScalar, T>); break;
+    case kChebBackward: e = w ? go(k_cheb<T, kChebBackward, double>) : go(k_cheb<T, kChebBackward, T>); break;
+    case kChebForwardT: e = go(k_cheb<T, kChebForwardT, T>); break;
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template cudaError_t launch_cheb<float>(int, int, bool, const void*, void*, int, long, const FftPlan&,
-                                        const float2*, const float2*, cudaStream_t);
+                                        const float2*, const float2*, cudaStream_t, bool);
 template cudaError_t launch_cheb<double>(int, int, bool, const void*, void*, int, long, const FftPlan&,
-                                         const double2*, const double2*, cudaStream_t);
+                                         const double2*, const double2*, cudaStream_t, bool);
 
 }  // namespace sgm

@@ -1,0 +1,258 @@
+// k_fast.cuh - the rows / strided / Chebyshev transform kernels on the compile-time FFT
+// engine (fft_fast.cuh).  Same arithmetic as k_fourier.cu and k_cheb.cu (whose comments give
+// the formulas); only the FFT length is a template parameter.  Included by k_fast_*.cu.
+#pragma once
+#include <algorithm>
+
+#include "convert.cuh"
+#include "fft_fast.cuh"
+
+namespace sgm {
+
+template <typename T> __host__ __device__ constexpr int fast_elems() { return sizeof(T) == 4 ? 4096 : 2048; }
+template <typename T> __host__ __device__ constexpr int fast_tw_cols() { return sizeof(T) == 4 ? 16 : 8; }
+constexpr int kFastThreads = 256;
+
+// ---------------------------------------------------------------------------------------------
+// rows of the contiguous last axis; LF = FFT length (L/2 for packed R2C/C2R, else L)
+template <typename T, int MODE, int LF>
+__global__ void __launch_bounds__(kFastThreads) k_rows_fast(const void* __restrict__ in, void* __restrict__ out,
+                                                            long nrows, int L, const cplx<T>* __restrict__ twf,
+                                                            const cplx<T>* __restrict__ tw_L) {
+  using C = cplx<T>;
+  constexpr int LINES = fast_elems<T>() / LF > 0 ? fast_elems<T>() / LF : 1;
+  constexpr int LDP = pad_ld(LF);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long row0 = (long)blockIdx.x * LINES;
+  const int nl = (int)min((long)LINES, nrows - row0);
+  constexpr int H = LF;                                           // packed: L/2
+
+  if (MODE == kRowC2R) {
+    const C* src = reinterpret_cast<const C*>(in) + row0 * (H + 1);
+    for (int idx = threadIdx.x; idx < nl * H; idx += kFastThreads) {
+      const int line = idx / H, k = idx - line * H;
+      C x = src[(long)line * (H + 1) + k];
+      C y = src[(long)line * (H + 1) + (H - k)];
+      if (k == 0) { x.y = 0; y.y = 0; }
+      const C yc = cconj(y);
+      const C e = cadd(x, yc);
+      const C o = cmulc(csub(x, yc), __ldg(&tw_L[k]));
+      buf[line * LDP + padi(k)] = mk<C>(e.x - o.y, e.y + o.x);
+    }
+  } else {
+    const C* src = reinterpret_cast<const C*>(in) + row0 * LF;   // packed real rows are LF complex
+    for (int idx = threadIdx.x; idx < nl * LF; idx += kFastThreads) {
+      const int line = idx / LF, e = idx - line * LF;
+      buf[line * LDP + padi(e)] = src[idx];
+    }
+  }
+  __syncthreads();
+  constexpr bool INV = (MODE == kRowC2R || MODE == kRowC2CInv);
+  fft_fast<LF, LINES, kFastThreads, INV>(buf, nl, twf);
+
+  if (MODE == kRowR2C) {
+    C* dst = reinterpret_cast<C*>(out) + row0 * (H + 1);
+    const T s = (T)0.5 / (T)L;
+    for (int idx = threadIdx.x; idx < nl * (H + 1); idx += kFastThreads) {
+      const int line = idx / (H + 1), k = idx - line * (H + 1);
+      const C z = buf[line * LDP + padi(k == H ? 0 : k)];
+      const C zc = cconj(buf[line * LDP + padi(k == 0 ? 0 : H - k)]);
+      const C e = cadd(z, zc);
+      const C o = rot90<false>(cmul(__ldg(&tw_L[k]), csub(z, zc)));
+      dst[idx] = cscale(cadd(e, o), s);
+    }
+  } else {
+    C* dst = reinterpret_cast<C*>(out) + row0 * LF;
+    const T s = (MODE == kRowC2CFwd) ? (T)1 / (T)L : (T)1;
+    for (int idx = threadIdx.x; idx < nl * LF; idx += kFastThreads) {
+      const int line = idx / LF, e = idx - line * LF;
+      dst[idx] = (MODE == kRowC2CFwd) ? cscale(buf[line * LDP + padi(e)], s) : buf[line * LDP + padi(e)];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// strided axis of a [outer][L][inner] complex array, TW neighbouring columns per CTA
+template <typename T, bool INV, int L>
+__global__ void __launch_bounds__(kFastThreads) k_strided_fast(const cplx<T>* in, cplx<T>* out, long inner,
+                                                               const cplx<T>* __restrict__ twf) {
+  using C = cplx<T>;
+  constexpr int TW = fast_tw_cols<T>();
+  constexpr int LDP = pad_ld(L);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long o = blockIdx.y;
+  const long t0 = (long)blockIdx.x * TW;
+  const int nt = (int)min((long)TW, inner - t0);
+  const C* src = in + o * L * inner + t0;
+  C* dst = out + o * L * inner + t0;
+  for (int idx = threadIdx.x; idx < L * TW; idx += kFastThreads) {
+    const int i = idx / TW, t = idx % TW;
+    if (t < nt) buf[t * LDP + padi(i)] = src[(long)i * inner + t];
+  }
+  __syncthreads();
+  fft_fast<L, TW, kFastThreads, INV>(buf, nt, twf);
+  const T s = INV ? (T)1 : (T)1 / (T)L;
+  for (int idx = threadIdx.x; idx < L * TW; idx += kFastThreads) {
+    const int i = idx / TW, t = idx % TW;
+    if (t < nt) dst[(long)i * inner + t] = INV ? buf[t * LDP + padi(i)] : cscale(buf[t * LDP + padi(i)], s);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Chebyshev axis (see k_cheb.cu for the DCT-via-FFT formulas and the stencils)
+template <typename T> __device__ __forceinline__ T fbeta(int k) { return (T)(-2 * (k + 2)) / (T)(k + 3); }
+template <typename T> __device__ __forceinline__ T fgamma(int k) { return (T)(k + 1) / (T)(k + 3); }
+
+template <typename T, int MODE, typename TS, int N>
+__global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restrict__ in, void* __restrict__ out,
+                                                            long inner, int basis, int real,
+                                                            const cplx<T>* __restrict__ twf,
+                                                            const cplx<T>* __restrict__ dctw) {
+  using C = cplx<T>;
+  constexpr int TW = fast_tw_cols<T>();
+  constexpr int LDP = pad_ld(N);
+  constexpr int PER = (N * TW + kFastThreads - 1) / kFastThreads;   // elements per thread
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const long t0 = (long)blockIdx.x * TW;
+  const int nt = (int)min((long)TW, inner - t0);
+  const int nb = basis == kDirichlet ? N - 2 : (basis == kBiharmonic ? N - 4 : N);
+  auto reord = [](int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); };
+
+  if (MODE == kChebScalar || MODE == kChebForwardT) {
+    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
+      const int j = idx / TW, t = idx % TW;
+      if (t < nt) {
+        const long g = (long)j * inner + t0 + t;
+        const C v = real ? mk<C>(reinterpret_cast<const T*>(in)[g], (T)0) : reinterpret_cast<const C*>(in)[g];
+        buf[t * LDP + padi(reord(j))] = v;
+      }
+    }
+    __syncthreads();
+    fft_fast<N, TW, kFastThreads, false>(buf, nt, twf);
+    // moments, computed in registers and written back in place
+    const T scale = (MODE == kChebScalar) ? (T)3.14159265358979323846 / (T)N : (T)2 / (T)N;
+    C m[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) {
+        const C v = buf[t * LDP + padi(k)];
+        const C vr = cconj(buf[t * LDP + padi(k == 0 ? 0 : N - k)]);
+        const C w = __ldg(&dctw[k]);
+        const C a = cadd(v, vr), b = csub(v, vr);
+        T sc = scale;
+        if (MODE == kChebForwardT && k == 0) sc *= (T)0.5;
+        m[q] = mk<C>((T)0.5 * sc * (w.x * a.x - w.y * a.y), (T)0.5 * sc * (w.x * b.y + w.y * b.x));
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) buf[t * LDP + padi(k)] = m[q];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
+      const int k = idx / TW, t = idx % TW;
+      if (t >= nt) continue;
+      const C* mm = buf + t * LDP;
+      C s = mk<C>((T)0, (T)0);
+      if (k < nb) {
+        if (MODE == kChebForwardT || basis == kCheb) {
+          s = mm[padi(k)];
+        } else if (basis == kDirichlet) {
+          s = csub(mm[padi(k)], mm[padi(k + 2)]);
+        } else {
+          const T be = fbeta<T>(k), ga = fgamma<T>(k);
+          const C a0 = mm[padi(k)], a2 = mm[padi(k + 2)], a4 = mm[padi(k + 4)];
+          s = mk<C>(a0.x + be * a2.x + ga * a4.x, a0.y + be * a2.y + ga * a4.y);
+        }
+      }
+      const long g = (long)k * inner + t0 + t;
+      if (MODE == kChebForwardT) {
+        if (real) reinterpret_cast<T*>(out)[g] = s.x; else reinterpret_cast<C*>(out)[g] = s;
+      } else {
+        to_spec<TS, C>(reinterpret_cast<TS*>(out), g, real, s);
+      }
+    }
+  } else {  // backward
+    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
+      const int k = idx / TW, t = idx % TW;
+      if (t < nt) {
+        const C v = (k < nb) ? from_spec<TS, C>(reinterpret_cast<const TS*>(in), (long)k * inner + t0 + t, real)
+                             : mk<C>((T)0, (T)0);
+        buf[t * LDP + padi(k)] = v;
+      }
+    }
+    __syncthreads();
+    C a[PER];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) {
+        const C* c = buf + t * LDP;
+        C v = c[padi(k)];
+        if (basis == kDirichlet) {
+          if (k >= 2) v = csub(v, c[padi(k - 2)]);
+        } else if (basis == kBiharmonic) {
+          if (k >= 2) { const T be = fbeta<T>(k - 2); const C u = c[padi(k - 2)]; v.x += be * u.x; v.y += be * u.y; }
+          if (k >= 4) { const T ga = fgamma<T>(k - 4); const C u = c[padi(k - 4)]; v.x += ga * u.x; v.y += ga * u.y; }
+        }
+        a[q] = v;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) buf[t * LDP + padi(k)] = a[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) {
+        const C* c = buf + t * LDP;
+        if (k == 0) {
+          a[q] = c[padi(0)];
+        } else {
+          const C x = c[padi(k)], y = c[padi(N - k)];
+          const C d = mk<C>(x.x + y.y, x.y - y.x);
+          a[q] = cscale(cmulc(d, __ldg(&dctw[k])), (T)0.5);
+        }
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = idx / N, k = idx % N;
+      if (t < nt) buf[t * LDP + padi(k)] = a[q];
+    }
+    __syncthreads();
+    fft_fast<N, TW, kFastThreads, true>(buf, nt, twf);
+    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
+      const int j = idx / TW, t = idx % TW;
+      if (t < nt) {
+        const C v = buf[t * LDP + padi(reord(j))];
+        const long g = (long)j * inner + t0 + t;
+        if (real) reinterpret_cast<T*>(out)[g] = v.x; else reinterpret_cast<C*>(out)[g] = v;
+      }
+    }
+  }
+}
+
+template <typename K> inline cudaError_t fast_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  return cudaSuccess;
+}
+
+}  // namespace sgm

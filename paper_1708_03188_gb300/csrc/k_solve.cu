@@ -25,210 +25,390 @@
 //   right]; each row eliminates its two sub-diagonal entries against the two reduced rows
 //   above it.
 //
-// The per-row reduced quantities are written to a global FP64 scratch laid out
-// [row][value][thread] (a warp's 32 threads touch 256 contiguous bytes) and read back by
-// the back substitution.  Warps own 32 neighbouring columns of one parity, so every load
-// and store of a row is coalesced.  Reciprocals: an FP32 seed refined by two
-// Newton-Raphson steps in FP64 (r <- r + r (1 - x r)), each squaring the relative error.
+// Work decomposition.  On a 3-D space the columns with Fourier indices (l1, l2) and
+// (-l1, l2) have the same kappa2 and hence the same matrix, so one thread eliminates the
+// pair (NC = 2): the FP64 factorisation (pivots, reciprocals, tail coefficients) is shared
+// and only the right-hand-side recurrences are done per column.  Columns l1 = 0 and
+// l1 = -M1/2 have no partner and are solved as a pair of identical columns.  Warps own 32
+// consecutive work items of one parity, so every load and store of a row is coalesced.
+// The per-row reduced quantities go to a global FP64 scratch laid out [row][value][thread]
+// (a warp touches 256 contiguous bytes) and are read back by the back substitution.
+// Coefficient tables are pre-multiplied by the call's scalars into shared memory.
+// Each sweep loads the next row's operands one row ahead, so the global-memory latency
+// overlaps the FP64 work of the current row.
+// Reciprocals: the PTX approximate FP64 reciprocal refined by one third-order Newton step
+// (r <- r + r (e + e^2), e = 1 - x r), which cubes the relative error.  FP32 data is
+// widened and narrowed on the integer pipe (convert.cuh).
 #include <algorithm>
 
 #include "common.cuh"
+#include "convert.cuh"
 
 namespace sgm {
 
 __device__ __forceinline__ double rcp64(double x) {
-  const float xf = (float)x;
-  const float ax = fabsf(xf);
-  if (!(ax > 1e-36f && ax < 1e36f)) return 1.0 / x;
-  double r = (double)__frcp_rn(xf);
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  return fma(r, e, r);
+  // seed: PTX rcp.approx.ftz.f64 (relative error below 2^-22 for normal x); one cubic
+  // Newton step r (1 + e + e^2), e = 1 - x r, takes the error to its cube (< 2^-66).
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 template <typename T> __device__ __forceinline__ double2 ld2(const void* p, long i, bool real) {
-  if (real) return make_double2((double)reinterpret_cast<const T*>(p)[i], 0.0);
+  if (real) return make_double2(widen<T>(reinterpret_cast<const T*>(p)[i]), 0.0);
   const cplx<T> v = reinterpret_cast<const cplx<T>*>(p)[i];
-  return make_double2((double)v.x, (double)v.y);
+  return make_double2(widen<T>(v.x), widen<T>(v.y));
 }
 template <typename T> __device__ __forceinline__ void st2(void* p, long i, bool real, double2 v) {
-  if (real) { reinterpret_cast<T*>(p)[i] = (T)v.x; return; }
-  cplx<T> w; w.x = (T)v.x; w.y = (T)v.y;
+  if (real) { reinterpret_cast<T*>(p)[i] = narrow<T>(v.x); return; }
+  cplx<T> w; w.x = narrow<T>(v.x); w.y = narrow<T>(v.y);
   reinterpret_cast<cplx<T>*>(p)[i] = w;
 }
 
-// table indices
+// Column mapping: work item w -> columns (c1, c2).  pair_m1 = 0: c1 = c2 = w (NC = 1).
+// Otherwise (3-D): axis 1 has M1 = pair_m1 entries; group g = w / n2 picks i1 = g for
+// g <= (M1-1)/2 paired with M1 - g, and i1 = M1/2 (even M1) alone.
+struct ColumnMap {
+  long nitems;
+  int pair_m1;
+  int n2;
+};
+
+__device__ __forceinline__ void map_columns(const ColumnMap& m, long w, long& c1, long& c2) {
+  if (m.pair_m1 == 0) { c1 = c2 = w; return; }
+  const long g = w / m.n2;
+  const long i2 = w - g * m.n2;
+  const int npairs = (m.pair_m1 - 1) / 2;
+  long i1, j1;
+  if (g == 0) { i1 = j1 = 0; }
+  else if (g <= npairs) { i1 = g; j1 = m.pair_m1 - g; }
+  else { i1 = j1 = m.pair_m1 / 2; }
+  c1 = i1 * m.n2 + i2;
+  c2 = j1 * m.n2 + i2;
+}
+
+// table indices (layout written by space.cu)
 enum { TD_B0 = 0, TD_A0 = 1, TD_G = 2, TD_COUNT = 3 };
 enum { TB_B0 = 0, TB_B2, TB_B4, TB_ALO, TB_A0, TB_AUP, TB_S0, TB_S1, TB_S2, TB_G0, TB_G1, TB_F0, TB_F1, TB_COUNT };
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict__ in, void* __restrict__ out, int N,
                                                          long ncols, int real, double a, double b,
                                                          const __grid_constant__ Wavenumbers wn,
+                                                         const __grid_constant__ ColumnMap cm,
                                                          const double* __restrict__ tab, int ts,
                                                          double* __restrict__ scratch) {
+  extern __shared__ double sh[];
+  double* aA0 = sh;        // a * A0_k
+  double* aG = sh + ts;    // a * G_k
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    aA0[k] = a * tab[TD_A0 * ts + k];
+    aG[k] = a * tab[TD_G * ts + k];
+  }
+  __syncthreads();
+  constexpr int NV = 2 + 2 * NC;
   const long nth = (long)gridDim.x * blockDim.x;
   const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const long nwarps_total = nth / 32;
-  const long ncb = (ncols + 31) / 32;
+  const long nwb = (cm.nitems + 31) / 32;
   const int nb = N - 2;
-  const double* B0 = tab + TD_B0 * ts;
-  const double* A0 = tab + TD_A0 * ts;
-  const double* G = tab + TD_G * ts;
-  for (long w = gt / 32; w < 2 * ncb; w += nwarps_total) {
+  const double half_pi = 1.5707963267948966;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
     const int p = (int)(w & 1);
-    const long c = (w >> 1) * 32 + lane;
-    if (c >= ncols) continue;
-    const double k2 = kappa2_of(wn, c);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[2];
+    map_columns(cm, item, cc[0], cc[1]);
+    const double k2 = kappa2_of(wn, cc[0]);
     const double aB = b - a * k2;
-    const double ell = -aB * 1.5707963267948966;
+    const double ell = -aB * half_pi;
+    const double aBpi = aB * 3.141592653589793;   // aB * B0_k for k > 0
     const int n = (nb - p + 1) / 2;
-    double pr = 0.0, pg = 0.0;
-    double2 pf = make_double2(0.0, 0.0);
+    double pr = 0.0, pge = 0.0, pg = 0.0;
+    double2 pf[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pf[q] = make_double2(0.0, 0.0);
+    // element offsets of row p of each column, and the stride of two rows
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    const long rstep = 2 * ncols;
+    double2 fn[NC];   // right-hand side of the next row, loaded one row ahead
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fn[q] = n > 0 ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+    double* s = scratch + gt;
+    const long sstep = (long)NV * nth;
     for (int i = 0; i < n; ++i) {
       const int k = p + 2 * i;
-      double2 f = ld2<T>(in, (long)k * ncols + c, real);
-      double d = fma(a, __ldg(&A0[k]), aB * __ldg(&B0[k]));
-      double g = a * __ldg(&G[k]);
+      double2 f[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q] = fn[q];
+        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+      }
+      double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
+      double g = aG[k];
       if (i > 0) {
         const double mu = ell * pr;
-        d = fma(-mu, pg + ell, d);
+        d = fma(-mu, pge, d);
         g = fma(-mu, pg, g);
-        f.x = fma(-mu, pf.x, f.x);
-        f.y = fma(-mu, pf.y, f.y);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f[q].x = fma(-mu, pf[q].x, f[q].x);
+          f[q].y = fma(-mu, pf[q].y, f[q].y);
+        }
       }
       const double r = rcp64(d);
-      double* s = scratch + (long)i * 4 * nth + gt;
       s[0] = r;
       s[nth] = g;
-      s[2 * nth] = f.x;
-      s[3 * nth] = f.y;
-      pr = r; pg = g; pf = f;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        s[(2 + 2 * q) * nth] = f[q].x;
+        s[(3 + 2 * q) * nth] = f[q].y;
+        pf[q] = f[q];
+      }
+      s += sstep;
+      pr = r; pg = g; pge = g + ell;
     }
-    double2 un = make_double2(0.0, 0.0), Ts = make_double2(0.0, 0.0);
+    double2 un[NC], Ts[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { un[q] = make_double2(0.0, 0.0); Ts[q] = make_double2(0.0, 0.0); }
+    double vn[NV];   // reduced row i, loaded one row ahead
+    s -= sstep;      // row n-1
+    if (n > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) vn[v] = s[v * nth];
+    }
     for (int i = n - 1; i >= 0; --i) {
       const int k = p + 2 * i;
-      const double* s = scratch + (long)i * 4 * nth + gt;
-      const double r = s[0], g = s[nth];
-      Ts.x += un.x; Ts.y += un.y;
-      double2 u;
-      u.x = (s[2 * nth] - ell * un.x - g * Ts.x) * r;
-      u.y = (s[3 * nth] - ell * un.y - g * Ts.y) * r;
-      st2<T>(out, (long)k * ncols + c, real, u);
-      un = u;
+      double v[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[j] = vn[j];
+      if (i > 0) {
+        s -= sstep;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
+      }
+      const double r = v[0], g = v[1];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        Ts[q].x += un[q].x;
+        Ts[q].y += un[q].y;
+        double2 u;
+        u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
+        u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
+        st2<T>(out, off[q] + (long)i * rstep, real, u);
+        un[q] = u;
+      }
     }
-    for (int k = nb + p; k < N; k += 2) st2<T>(out, (long)k * ncols + c, real, make_double2(0.0, 0.0));
+    for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+    }
   }
 }
 
-template <typename T>
+template <typename T, int NC>
 __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict__ in, void* __restrict__ out,
                                                           int N, long ncols, int real, double a, double b,
-                                                          double cc, const __grid_constant__ Wavenumbers wn,
+                                                          double cc0, const __grid_constant__ Wavenumbers wn,
+                                                          const __grid_constant__ ColumnMap cm,
                                                           const double* __restrict__ tab, int ts,
                                                           double* __restrict__ scratch) {
+  // shared tables: a*S0, a*S1, a*S2, a*G0, a*G1 and the unscaled B0, B2, B4, Alo, A0, Aup, F0, F1
+  extern __shared__ double sh[];
+  enum { SS0 = 0, SS1, SS2, SG0, SG1, SB0, SB2, SB4, SALO, SA0, SAUP, SF0, SF1, SCOUNT };
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    sh[SS0 * ts + k] = a * tab[TB_S0 * ts + k];
+    sh[SS1 * ts + k] = a * tab[TB_S1 * ts + k];
+    sh[SS2 * ts + k] = a * tab[TB_S2 * ts + k];
+    sh[SG0 * ts + k] = a * tab[TB_G0 * ts + k];
+    sh[SG1 * ts + k] = a * tab[TB_G1 * ts + k];
+    sh[SB0 * ts + k] = tab[TB_B0 * ts + k];
+    sh[SB2 * ts + k] = tab[TB_B2 * ts + k];
+    sh[SB4 * ts + k] = tab[TB_B4 * ts + k];
+    sh[SALO * ts + k] = tab[TB_ALO * ts + k];
+    sh[SA0 * ts + k] = tab[TB_A0 * ts + k];
+    sh[SAUP * ts + k] = tab[TB_AUP * ts + k];
+    sh[SF0 * ts + k] = tab[TB_F0 * ts + k];
+    sh[SF1 * ts + k] = tab[TB_F1 * ts + k];
+  }
+  __syncthreads();
+  auto tb = [&](int t, int k) -> double { return sh[t * ts + k]; };
+  constexpr int NV = 5 + 2 * NC;
   const long nth = (long)gridDim.x * blockDim.x;
   const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const long nwarps_total = nth / 32;
-  const long ncb = (ncols + 31) / 32;
+  const long nwb = (cm.nitems + 31) / 32;
   const int nb = N - 4;
-  auto tb = [&](int t, int k) -> double { return __ldg(&tab[t * ts + k]); };
-  for (long w = gt / 32; w < 2 * ncb; w += nwarps_total) {
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
     const int p = (int)(w & 1);
-    const long c = (w >> 1) * 32 + lane;
-    if (c >= ncols) continue;
-    const double k2 = kappa2_of(wn, c);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[2];
+    map_columns(cm, item, cc[0], cc[1]);
+    const double k2 = kappa2_of(wn, cc[0]);
     const double aA = b - 2.0 * a * k2;
-    const double aB = fma(a * k2, k2, fma(-b, k2, cc));
+    const double aB = fma(a * k2, k2, fma(-b, k2, cc0));
     const int n = (nb - p + 1) / 2;
-    // reduced rows i-1 (suffix 1) and i-2 (suffix 2)
-    double r1 = 0, U11 = 0, U21 = 0, g01 = 0, g11 = 0;
-    double r2 = 0, U12 = 0, U22 = 0, g02 = 0, g12 = 0;
-    double2 f1 = make_double2(0, 0), f2 = make_double2(0, 0);
+    // reduced rows i-1 (suffix 1) and i-2 (suffix 2); q4 = aB * B4 of rows i-1, i-2
+    double r1 = 0, U11 = 0, U21 = 0, g01 = 0, g11 = 0, q41 = 0;
+    double r2 = 0, U12 = 0, U22 = 0, g02 = 0, g12 = 0, q42 = 0;
+    double2 f1[NC], f2[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { f1[q] = make_double2(0, 0); f2[q] = make_double2(0, 0); }
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    const long rstep = 2 * ncols;
+    double2 fn[NC];   // right-hand side of the next row, loaded one row ahead
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fn[q] = n > 0 ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+    double* s = scratch + gt;
+    const long sstep = (long)NV * nth;
     for (int i = 0; i < n; ++i) {
       const int k = p + 2 * i;
-      double2 f = ld2<T>(in, (long)k * ncols + c, real);
-      double D = fma(a, tb(TB_S0, k), fma(aA, tb(TB_A0, k), aB * tb(TB_B0, k)));
-      double u1 = fma(a, tb(TB_S1, k), fma(aA, tb(TB_AUP, k), aB * tb(TB_B2, k)));
-      double u2 = fma(a, tb(TB_S2, k), aB * tb(TB_B4, k));
-      double h0 = a * tb(TB_G0, k), h1 = a * tb(TB_G1, k);
-      const double F0a = tb(TB_F0, k + 2), F1a = tb(TB_F1, k + 2);
-      const double F0b = tb(TB_F0, k + 4), F1b = tb(TB_F1, k + 4);
-      if (i >= 2) {
-        double L1 = fma(aA, tb(TB_ALO, k), aB * tb(TB_B2, k - 2));
-        const double mu = aB * tb(TB_B4, k - 4) * r2;
-        L1 = fma(-mu, U12, L1);
-        D = fma(-mu, U22, D);
-        u1 = fma(-mu, fma(g02, F0a, g12 * F1a), u1);
-        u2 = fma(-mu, fma(g02, F0b, g12 * F1b), u2);
-        h0 = fma(-mu, g02, h0);
-        h1 = fma(-mu, g12, h1);
-        f.x = fma(-mu, f2.x, f.x);
-        f.y = fma(-mu, f2.y, f.y);
-        const double mu1 = L1 * r1;
+      double2 f[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q] = fn[q];
+        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+      }
+      const double q4 = aB * tb(SB4, k);
+      double D = fma(aA, tb(SA0, k), fma(aB, tb(SB0, k), tb(SS0, k)));
+      double u1 = fma(aA, tb(SAUP, k), fma(aB, tb(SB2, k), tb(SS1, k)));
+      double u2 = tb(SS2, k) + q4;
+      double h0 = tb(SG0, k), h1 = tb(SG1, k);
+      const double F0a = tb(SF0, k + 2), F1a = tb(SF1, k + 2);
+      const double F0b = tb(SF0, k + 4), F1b = tb(SF1, k + 4);
+      if (i >= 1) {
+        double L1 = fma(aA, tb(SALO, k), aB * tb(SB2, k - 2));
+        double mu1;
+        if (i >= 2) {
+          const double mu = q42 * r2;
+          L1 = fma(-mu, U12, L1);
+          D = fma(-mu, U22, D);
+          u1 = fma(-mu, fma(g02, F0a, g12 * F1a), u1);
+          u2 = fma(-mu, fma(g02, F0b, g12 * F1b), u2);
+          h0 = fma(-mu, g02, h0);
+          h1 = fma(-mu, g12, h1);
+#pragma unroll
+          for (int q = 0; q < NC; ++q) {
+            f[q].x = fma(-mu, f2[q].x, f[q].x);
+            f[q].y = fma(-mu, f2[q].y, f[q].y);
+          }
+        }
+        mu1 = L1 * r1;
         D = fma(-mu1, U11, D);
         u1 = fma(-mu1, U21, u1);
         u2 = fma(-mu1, fma(g01, F0b, g11 * F1b), u2);
         h0 = fma(-mu1, g01, h0);
         h1 = fma(-mu1, g11, h1);
-        f.x = fma(-mu1, f1.x, f.x);
-        f.y = fma(-mu1, f1.y, f.y);
-      } else if (i == 1) {
-        const double L1 = fma(aA, tb(TB_ALO, k), aB * tb(TB_B2, k - 2));
-        const double mu1 = L1 * r1;
-        D = fma(-mu1, U11, D);
-        u1 = fma(-mu1, U21, u1);
-        u2 = fma(-mu1, fma(g01, F0b, g11 * F1b), u2);
-        h0 = fma(-mu1, g01, h0);
-        h1 = fma(-mu1, g11, h1);
-        f.x = fma(-mu1, f1.x, f.x);
-        f.y = fma(-mu1, f1.y, f.y);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f[q].x = fma(-mu1, f1[q].x, f[q].x);
+          f[q].y = fma(-mu1, f1[q].y, f[q].y);
+        }
       }
       const double r = rcp64(D);
-      double* s = scratch + (long)i * 7 * nth + gt;
       s[0] = r; s[nth] = u1; s[2 * nth] = u2; s[3 * nth] = h0; s[4 * nth] = h1;
-      s[5 * nth] = f.x; s[6 * nth] = f.y;
-      r2 = r1; U12 = U11; U22 = U21; g02 = g01; g12 = g11; f2 = f1;
-      r1 = r; U11 = u1; U21 = u2; g01 = h0; g11 = h1; f1 = f;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        s[(5 + 2 * q) * nth] = f[q].x;
+        s[(6 + 2 * q) * nth] = f[q].y;
+        f2[q] = f1[q];
+        f1[q] = f[q];
+      }
+      s += sstep;
+      r2 = r1; U12 = U11; U22 = U21; g02 = g01; g12 = g11; q42 = q41;
+      r1 = r; U11 = u1; U21 = u2; g01 = h0; g11 = h1; q41 = q4;
     }
-    double2 ua = make_double2(0, 0), ub = make_double2(0, 0), uc = make_double2(0, 0);  // u_{i+1}, u_{i+2}, u_{i+3}
-    double2 T0 = make_double2(0, 0), T1 = make_double2(0, 0);
+    // back substitution: u_{i+1}, u_{i+2}, u_{i+3} and the tail sums T0, T1 per column
+    double2 ua[NC], ub[NC], uc[NC], T0[NC], T1[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      ua[q] = ub[q] = uc[q] = make_double2(0, 0);
+      T0[q] = T1[q] = make_double2(0, 0);
+    }
+    double vn[NV];   // reduced row i, loaded one row ahead
+    s -= sstep;      // row n-1
+    if (n > 0) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) vn[v] = s[v * nth];
+    }
     for (int i = n - 1; i >= 0; --i) {
       const int k = p + 2 * i;
-      if (i + 3 < n) {
-        const double F0 = tb(TB_F0, k + 6), F1 = tb(TB_F1, k + 6);
-        T0.x = fma(F0, uc.x, T0.x); T0.y = fma(F0, uc.y, T0.y);
-        T1.x = fma(F1, uc.x, T1.x); T1.y = fma(F1, uc.y, T1.y);
+      const double F0 = tb(SF0, k + 6), F1 = tb(SF1, k + 6);   // zero past the basis
+      double v[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) v[j] = vn[j];
+      if (i > 0) {
+        s -= sstep;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
       }
-      const double* s = scratch + (long)i * 7 * nth + gt;
-      const double r = s[0], u1 = s[nth], u2 = s[2 * nth], h0 = s[3 * nth], h1 = s[4 * nth];
-      double2 u;
-      u.x = (s[5 * nth] - u1 * ua.x - u2 * ub.x - h0 * T0.x - h1 * T1.x) * r;
-      u.y = (s[6 * nth] - u1 * ua.y - u2 * ub.y - h0 * T0.y - h1 * T1.y) * r;
-      st2<T>(out, (long)k * ncols + c, real, u);
-      uc = ub; ub = ua; ua = u;
+      const double r = v[0], u1 = v[1], u2 = v[2], h0 = v[3], h1 = v[4];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        T0[q].x = fma(F0, uc[q].x, T0[q].x); T0[q].y = fma(F0, uc[q].y, T0[q].y);
+        T1[q].x = fma(F1, uc[q].x, T1[q].x); T1[q].y = fma(F1, uc[q].y, T1[q].y);
+        double2 u;
+        u.x = fma(-h1, T1[q].x, fma(-h0, T0[q].x, fma(-u2, ub[q].x, fma(-u1, ua[q].x, v[5 + 2 * q])))) * r;
+        u.y = fma(-h1, T1[q].y, fma(-h0, T0[q].y, fma(-u2, ub[q].y, fma(-u1, ua[q].y, v[6 + 2 * q])))) * r;
+        st2<T>(out, off[q] + (long)i * rstep, real, u);
+        uc[q] = ub[q]; ub[q] = ua[q]; ua[q] = u;
+      }
     }
-    for (int k = nb + p; k < N; k += 2) st2<T>(out, (long)k * ncols + c, real, make_double2(0.0, 0.0));
+    for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+    }
   }
 }
+
+// Values per row per thread in the scratch (NC = 2 upper bound).
+int solve_scratch_values(int basis) { return basis == kDirichlet ? 6 : 9; }
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
                          long ncols, const Wavenumbers& wn, const double* tab, double* scratch,
                          long scratch_threads, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
-  const long warps_needed = 2 * ((ncols + 31) / 32);
+  ColumnMap cm;
+  cm.pair_m1 = 0;
+  cm.n2 = wn.n2;
+  cm.nitems = ncols;
+  if (wn.n1 > 1) {  // 3-D: pair +l1 / -l1 along axis 1
+    cm.pair_m1 = wn.n1;
+    const long groups = 1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0);
+    cm.nitems = groups * wn.n2;
+  }
+  const long warps_needed = 2 * ((cm.nitems + 31) / 32);
   long threads = std::min(scratch_threads, warps_needed * 32);
   threads = std::max(128L, (threads / 128) * 128);
   const unsigned grid = (unsigned)(threads / 128);
   const int ts = N + 8;
-  if (basis == kDirichlet)
-    k_solve_dirichlet<T><<<grid, 128, 0, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, tab, ts, scratch);
-  else
-    k_solve_biharmonic<T><<<grid, 128, 0, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, tab, ts, scratch);
+  cudaError_t e;
+  if (basis == kDirichlet) {
+    const size_t smem = sizeof(double) * 2 * ts;
+    if (cm.pair_m1) {
+      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+      k_solve_dirichlet<T, 2><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    } else {
+      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+      k_solve_dirichlet<T, 1><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    }
+  } else {
+    const size_t smem = sizeof(double) * 13 * ts;
+    if (cm.pair_m1) {
+      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+      k_solve_biharmonic<T, 2><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
+    } else {
+      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+      k_solve_biharmonic<T, 1><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
+    }
+  }
   return cudaGetLastError();
 }
 

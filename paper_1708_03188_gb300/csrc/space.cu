@@ -20,6 +20,7 @@
 
 #include "../../include/sgm.h"
 #include "common.cuh"
+#include "fft_fast.cuh"
 
 using namespace sgm;
 
@@ -95,6 +96,7 @@ struct sgm_space {
   long nphys = 0, nspec = 0;
   size_t phys_bytes = 0, spec_bytes = 0;
   std::map<int, void*> tw;   // length -> exp(-2 pi i k / L)
+  std::map<int, void*> twf;  // length -> pass twiddle tables of the compile-time FFT engine
   void* dctw = nullptr;      // exp(-i pi k / (2N))
   double* tab = nullptr;     // Galerkin coefficient tables (Dirichlet or biharmonic)
   void* W1 = nullptr;
@@ -126,6 +128,34 @@ int need_tw(sgm_space* s, int L) {
   int st = s->prec == SGM_F32 ? upload_twiddles<float>(s, L, &p) : upload_twiddles<double>(s, L, &p);
   if (st != SGM_OK) return st;
   s->tw[L] = p;
+  return SGM_OK;
+}
+
+template <typename T> int upload_fast_twiddles(int L, void** out) {
+  std::vector<cplx<T>> h(fast_table_size(L));
+  fill_fast_table(L, h.data(), [&](long j) {
+    const long double a = -2.0L * kPi * (long double)j / (long double)L;
+    cplx<T> w;
+    w.x = (T)cosl(a);
+    w.y = (T)sinl(a);
+    return w;
+  });
+  SGM_CU(cudaMalloc(out, sizeof(cplx<T>) * h.size()));
+  SGM_CU(cudaMemcpy(*out, h.data(), sizeof(cplx<T>) * h.size(), cudaMemcpyHostToDevice));
+  return SGM_OK;
+}
+
+// pass tables for the compile-time engine when L has a compiled kernel (else nullptr)
+int need_twf(sgm_space* s, int L, const void** out) {
+  *out = nullptr;
+  if (!fast_compiled(L)) return SGM_OK;
+  if (!s->twf.count(L)) {
+    void* p = nullptr;
+    int st = s->prec == SGM_F32 ? upload_fast_twiddles<float>(L, &p) : upload_fast_twiddles<double>(L, &p);
+    if (st != SGM_OK) return st;
+    s->twf[L] = p;
+  }
+  *out = s->twf[L];
   return SGM_OK;
 }
 
@@ -261,8 +291,15 @@ template <typename T> int fourier_forward(sgm_space* s, const void* in, void* ou
   FftPlan p = make_plan(fl);
   SGM_TRY(need_tw(s, fl));
   SGM_TRY(need_tw(s, L));
-  SGM_TRY(wrap(launch_rows<T>(r2c ? kRowR2C : kRowC2CFwd, in, out, nrows, L, p, (const cplx<T>*)s->tw[fl],
-                              (const cplx<T>*)s->tw[L], st), "rows forward"));
+  const void* twf = nullptr;
+  SGM_TRY(need_twf(s, fl, &twf));
+  const int mode = r2c ? kRowR2C : kRowC2CFwd;
+  if (twf && (!r2c || L % 2 == 0))
+    SGM_TRY(wrap(launch_rows_fast<T>(mode, in, out, nrows, L, (const cplx<T>*)twf, (const cplx<T>*)s->tw[L], st),
+                 "rows forward"));
+  else
+    SGM_TRY(wrap(launch_rows<T>(mode, in, out, nrows, L, p, (const cplx<T>*)s->tw[fl], (const cplx<T>*)s->tw[L], st),
+                 "rows forward"));
   for (int a = d - 1; a >= first_fourier(s); --a) {
     long outer = 1, inner = 1;
     for (int i = 0; i < a; ++i) outer *= s->spec[i];
@@ -270,8 +307,13 @@ template <typename T> int fourier_forward(sgm_space* s, const void* in, void* ou
     const int La = (int)s->n[a];
     FftPlan pa = make_plan(La);
     SGM_TRY(need_tw(s, La));
-    SGM_TRY(wrap(launch_strided<T>(false, out, out, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
-                 "strided forward"));
+    const void* twf = nullptr;
+    SGM_TRY(need_twf(s, La, &twf));
+    if (twf)
+      SGM_TRY(wrap(launch_strided_fast<T>(false, out, out, outer, La, inner, (const cplx<T>*)twf, st), "strided forward"));
+    else
+      SGM_TRY(wrap(launch_strided<T>(false, out, out, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
+                   "strided forward"));
   }
   return SGM_OK;
 }
@@ -288,8 +330,14 @@ template <typename T> int fourier_backward(sgm_space* s, const void* in, void* o
     const int La = (int)s->n[a];
     FftPlan pa = make_plan(La);
     SGM_TRY(need_tw(s, La));
-    SGM_TRY(wrap(launch_strided<T>(true, cur, s->W1, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
-                 "strided backward"));
+    const void* twf = nullptr;
+    SGM_TRY(need_twf(s, La, &twf));
+    if (twf)
+      SGM_TRY(wrap(launch_strided_fast<T>(true, cur, s->W1, outer, La, inner, (const cplx<T>*)twf, st),
+                   "strided backward"));
+    else
+      SGM_TRY(wrap(launch_strided<T>(true, cur, s->W1, outer, La, inner, pa, (const cplx<T>*)s->tw[La], st),
+                   "strided backward"));
     cur = s->W1;
   }
   const int L = (int)s->n[d];
@@ -300,19 +348,31 @@ template <typename T> int fourier_backward(sgm_space* s, const void* in, void* o
   FftPlan p = make_plan(fl);
   SGM_TRY(need_tw(s, fl));
   SGM_TRY(need_tw(s, L));
-  return wrap(launch_rows<T>(r2c ? kRowC2R : kRowC2CInv, cur, out, nrows, L, p, (const cplx<T>*)s->tw[fl],
-                             (const cplx<T>*)s->tw[L], st),
+  const void* twf = nullptr;
+  SGM_TRY(need_twf(s, fl, &twf));
+  const int mode = r2c ? kRowC2R : kRowC2CInv;
+  if (twf && (!r2c || L % 2 == 0))
+    return wrap(launch_rows_fast<T>(mode, cur, out, nrows, L, (const cplx<T>*)twf, (const cplx<T>*)s->tw[L], st),
+                "rows backward");
+  return wrap(launch_rows<T>(mode, cur, out, nrows, L, p, (const cplx<T>*)s->tw[fl], (const cplx<T>*)s->tw[L], st),
               "rows backward");
 }
 
-template <typename T> int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st) {
+template <typename T>
+int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide = false) {
   const int N = (int)s->n[0];
   long inner = 1;
   for (int i = 1; i < s->ndim; ++i) inner *= s->spec[i];
   FftPlan p = make_plan(N);
   SGM_TRY(need_tw(s, N));
+  const void* twf = nullptr;
+  SGM_TRY(need_twf(s, N, &twf));
+  if (twf)
+    return wrap(launch_cheb_fast<T>(mode, s->kinds[0], s->real_spec, in, out, N, inner, (const cplx<T>*)twf,
+                                    (const cplx<T>*)s->dctw, st, wide),
+                "chebyshev pass");
   return wrap(launch_cheb<T>(mode, s->kinds[0], s->real_spec, in, out, N, inner, p, (const cplx<T>*)s->tw[N],
-                             (const cplx<T>*)s->dctw, st),
+                             (const cplx<T>*)s->dctw, st, wide),
               "chebyshev pass");
 }
 
@@ -353,11 +413,13 @@ int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void
               "solve");
 }
 
-template <typename T> int scalar_impl(sgm_space* s, const void* f, void* out, cudaStream_t st, int mode) {
+// wide: write the spectral result in FP64 (FP32 spaces, internal intermediates only)
+template <typename T>
+int scalar_impl(sgm_space* s, const void* f, void* out, cudaStream_t st, int mode, bool wide = false) {
   if (!s->cheb) return fourier_forward<T>(s, f, out, st);
-  if (s->ndim == 1) return cheb_pass<T>(s, mode, f, out, st);
+  if (s->ndim == 1) return cheb_pass<T>(s, mode, f, out, st, wide);
   SGM_TRY(fourier_forward<T>(s, f, s->W1, st));
-  return cheb_pass<T>(s, mode, s->W1, out, st);
+  return cheb_pass<T>(s, mode, s->W1, out, st, wide);
 }
 
 template <typename T> int forward_impl(sgm_space* s, const void* u, void* out, cudaStream_t st) {
@@ -369,19 +431,19 @@ template <typename T> int forward_impl(sgm_space* s, const void* u, void* out, c
   return solve_impl<T>(s, kBiharmonic, 0.0, 0.0, 1.0, out, out, st);
 }
 
-template <typename T> int backward_impl(sgm_space* s, const void* uh, void* u, cudaStream_t st) {
-  if (!s->cheb) {
-    if (s->ndim == 1) return fourier_backward<T>(s, uh, u, st);
-    return fourier_backward<T>(s, uh, u, st);
-  }
-  if (s->ndim == 1) return cheb_pass<T>(s, kChebBackward, uh, u, st);
-  SGM_TRY(cheb_pass<T>(s, kChebBackward, uh, s->W1, st));
+// wide: the spectral input is FP64 (FP32 spaces, internal intermediates only)
+template <typename T> int backward_impl(sgm_space* s, const void* uh, void* u, cudaStream_t st, bool wide = false) {
+  if (!s->cheb) return fourier_backward<T>(s, uh, u, st);
+  if (s->ndim == 1) return cheb_pass<T>(s, kChebBackward, uh, u, st, wide);
+  SGM_TRY(cheb_pass<T>(s, kChebBackward, uh, s->W1, st, wide));
   return fourier_backward<T>(s, s->W1, u, st);
 }
 
 void free_space(sgm_space* s) {
   for (auto& kv : s->tw) cudaFree(kv.second);
   s->tw.clear();
+  for (auto& kv : s->twf) cudaFree(kv.second);
+  s->twf.clear();
   cudaFree(s->dctw);
   cudaFree(s->tab);
   cudaFree(s->W1);
@@ -473,7 +535,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   };
   const size_t wbytes = std::max(s->spec_bytes, (size_t)s->nspec * s->celem());
   chk(cudaMalloc(&s->W1, wbytes), "workspace");
-  chk(cudaMalloc(&s->W2, wbytes), "workspace");
+  // W2 holds the spectral intermediate of the physical-to-physical solves, in FP64
+  chk(cudaMalloc(&s->W2, (size_t)s->nspec * 16), "workspace");
   if (st == SGM_OK && cheb) {
     const int N = (int)n[0];
     st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);
@@ -486,7 +549,7 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       need = ((need + 127) / 128) * 128;
       s->scratch_threads = std::min((long)std::max(1, sms) * 256, need);
       const long rows = N / 2 + 1;
-      const int nv = kinds[0] == SGM_SHEN_DIRICHLET ? 4 : 7;
+      const int nv = solve_scratch_values(kinds[0] == SGM_SHEN_DIRICHLET ? kDirichlet : kBiharmonic);
       chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
     }
   }
@@ -560,12 +623,29 @@ int sgm_biharmonic_solve(sgm_space* s, double a, double b, double c, const void*
   return solve_entry(s, kBiharmonic, a, b, c, f_tilde, u_hat, stream);
 }
 
+// Physical -> physical: scalar product into W2 (FP64 spectral intermediate), FP64 solve in
+// place, backward from W2.  On FP32 spaces the transforms stay FP32 and only the
+// Chebyshev kernels widen/narrow the intermediate.
 static int full_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u, void* stream) {
   SGM_TRY(check_space(s));
+  if ((basis == kDirichlet && s->kinds[0] != SGM_SHEN_DIRICHLET) ||
+      (basis == kBiharmonic && s->kinds[0] != SGM_SHEN_BIHARMONIC))
+    return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
+  if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
+    return fail(SGM_ERR_ARG, "coefficients must be finite");
+  if (basis == kDirichlet && a == 0.0 && b == 0.0) return fail(SGM_ERR_ARG, "a = b = 0 gives a singular system");
+  if (basis == kBiharmonic && a == 0.0 && b == 0.0 && c == 0.0)
+    return fail(SGM_ERR_ARG, "a = b = c = 0 gives a singular system");
   SGM_TRY(check_ptrs(f, s->phys_bytes, u, s->phys_bytes, false));
-  SGM_TRY(sgm_scalar_product(s, f, s->W2, stream));
-  SGM_TRY(solve_entry(s, basis, a, b, c, s->W2, s->W2, stream));
-  return sgm_backward(s, s->W2, u, stream);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (s->prec == SGM_F32) {
+    SGM_TRY(scalar_impl<float>(s, f, s->W2, st, kChebScalar, true));
+    SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));
+    return backward_impl<float>(s, s->W2, u, st, true);
+  }
+  SGM_TRY(scalar_impl<double>(s, f, s->W2, st, kChebScalar));
+  SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));
+  return backward_impl<double>(s, s->W2, u, st);
 }
 
 int sgm_helmholtz(sgm_space* s, double a, double b, const void* f, void* u, void* stream) {

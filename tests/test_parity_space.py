@@ -88,6 +88,14 @@ SPACES = [
     (["c2c", "c2c", "c2c"], [6, 8, 5]),
     (["dirichlet", "r2c"], [4, 2]),            # smallest sizes
     (["biharmonic", "c2c"], [6, 1]),
+    # lengths with compile-time FFT kernels (2^a and 3 * 2^a), several tiles plus ragged tails
+    (["dirichlet", "c2c", "r2c"], [64, 256, 128]),
+    (["biharmonic", "c2c", "r2c"], [128, 32, 64]),
+    (["c2c", "c2c"], [768, 48]),
+    (["c2c", "r2c"], [192, 1536]),
+    (["chebyshev", "c2c"], [256, 19]),
+    (["dirichlet", "c2c"], [512, 24]),
+    (["biharmonic"], [384]),
 ]
 
 
