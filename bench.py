@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["f32", "f64"], default="f32")
+    p.add_argument("--gl-steps", type=int, default=200,
+                   help="time this many Ginzburg-Landau steps per variant (0: skip)")
     p.add_argument("--kernel", default=None,
                    choices=["helmholtz_solve", "biharmonic_solve", "scalar_product", "backward", "step"],
                    help="run only this call (warmup + steps times) for profiling; prints no bench line")
@@ -299,6 +301,8 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_ms = float(t.item())
 
+    gl = gl_measure(Space, stream, steps=args.gl_steps) if args.gl_steps > 0 else None
+
     value = world * DOF_PER_STEP / (ms * 1e-3) / 1e9
     line = None
     if rank == 0:
@@ -322,12 +326,44 @@ def run_ours(args):
             "gpu_launches": 14 * args.steps,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "gl": gl,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def gl_measure(Space, stream, M=512, steps=200):
+    """Ginzburg-Landau steps/s on M x M (Fourier 512^2, [-50,50]^2, 3/2-rule padding, beta=1.5,
+    gamma=-0.5, seeded u0 = 0.01 (N(0,1) + i N(0,1))); steps timed with CUDA events."""
+    import torch
+    from paper_1708_03188_gb300 import inputs
+    from paper_1708_03188_gb300.sgm import GinzburgLandau
+    out = {"grid": f"{M}^2", "padded": f"{3 * M // 2}^2", "beta": 1.5, "gamma": -0.5}
+    u0 = inputs.gl_initial(M)
+    for prec in ("f64", "f32"):
+        sp = Space(["c2c", "c2c"], (M, M), domain=[(-50.0, 50.0), (-50.0, 50.0)], precision=prec)
+        uphys = torch.from_numpy(u0).to(sp.physical_dtype).cuda()
+        for scheme, dt in (("ifrk4", 0.01), ("rk4", 0.0025)):
+            gl = GinzburgLandau(sp, 1.5, -0.5, dt, scheme)
+            u = sp.forward(uphys)
+            gl.step(u, 3)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            gl.step(u, steps)
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / steps
+            finite = bool(torch.isfinite(torch.view_as_real(u)).all().item())
+            out[f"{prec}_{scheme}_dt{dt}"] = {"steps_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 5),
+                                              "finite_after": finite, "launches_per_step": 12}
+            gl.close()
+        sp.close()
+    return out
 
 
 # ---- FP64 CPU oracle on a bounded sample of the same workload ---------------------------------------

@@ -162,6 +162,32 @@ int sgm_helmholtz(sgm_space* space, double a, double b, const void* f, void* u, 
 int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f, void* u,
                    void* stream);
 
+/* ---- complex Ginzburg-Landau equation (Sec. 6 of the paper) ------------------------------- */
+#define SGM_GL_RK4 0      /* explicit classical RK4, the paper's time loop */
+#define SGM_GL_IFRK4 1    /* classical RK4 on exp(-L t) u_hat (linear part integrated exactly) */
+
+typedef struct sgm_gl sgm_gl;
+
+/*
+ * Create a stepper for  u_t = u + (1 + i beta) lap(u) - (1 + i gamma) |u|^2 u  on the space
+ * (a square M x M SGM_FOURIER_C2C x SGM_FOURIER_C2C space; M in {32, 64, ..., 1024}; equal
+ * domain lengths, e.g. [-50, 50]^2 as in Sec. 6).  The paper's equation is beta = 0,
+ * gamma = 1.5.  In Fourier space du_hat/dt = L(k) u_hat - N(u_hat), L(k) = 1 - (1 + i beta)|k|^2,
+ * with the nonlinear term N evaluated with the padded transforms of Sec. 6: padding must be
+ * 1.5 (coefficients copied to an (3M/2)^2 array at the same wavenumbers, zero elsewhere;
+ * backward transform unscaled; forward transform with 1/(3M/2) per axis, truncated).
+ * dt > 0; scheme SGM_GL_RK4 or SGM_GL_IFRK4.  Precision follows the space (SGM_F32: complex64
+ * state and FP32 arithmetic; SGM_F64: complex128 and FP64).  The space may be destroyed
+ * after this call; the stepper owns its workspaces and tables.
+ */
+int sgm_gl_create(sgm_gl** out, const sgm_space* space, double padding, double beta, double gamma,
+                  double dt, int scheme);
+int sgm_gl_destroy(sgm_gl* gl);
+/* rhs = L(k) u_hat - N(u_hat) for a spectral M x M state u_hat (FFT order on both axes). */
+int sgm_gl_rhs(sgm_gl* gl, const void* u_hat, void* rhs, void* stream);
+/* Advance u_hat (in place) by nsteps time steps of the stepper's scheme. */
+int sgm_gl_step(sgm_gl* gl, void* u_hat, int nsteps, void* stream);
+
 /*
  * Dirichlet Helmholtz solve that allocates nothing (no counterpart in the paper; it is an
  * interface choice of this library).

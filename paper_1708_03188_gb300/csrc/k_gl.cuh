@@ -1,0 +1,239 @@
+// k_gl.cuh - complex Ginzburg-Landau right-hand side with the 3/2-rule padded nonlinear term
+// (Sec. 6 of the paper) and the RK4 stage updates, on an M x M doubly periodic grid.
+//
+// Equation (general form; the paper's is beta = 0, gamma = 1.5):
+//     u_t = u + (1 + i beta) lap(u) - (1 + i gamma) |u|^2 u,
+// in Fourier space  du_hat/dt = L(k) u_hat - N(u_hat),  L(k) = 1 - (1 + i beta) |k|^2 with
+// k = 2 pi l / length on each axis.  N(u_hat) is the padded product of Sec. 6: the
+// coefficients are copied to an Mp x Mp array (Mp = 3M/2) at the same wavenumbers, zero
+// elsewhere, transformed back without scaling, multiplied pointwise by (1 + i gamma)|u|^2,
+// transformed forward with 1/Mp per axis and truncated to the original wavenumber set.
+//
+// Three kernels per right-hand side, all on the compile-time FFT engine of length Mp:
+//   K1 k_gl_rows_pad   each of the M spectral rows: zero-pad to Mp, inverse FFT along the
+//                      row -> P (M x Mp); the padded rows are zero and never stored.
+//   K2 k_gl_cols       each column of P (TW columns per CTA): place the M values at their
+//                      padded positions, inverse FFT along the column, pointwise nonlinear
+//                      product, forward FFT, keep the M original positions (x 1/Mp), in place.
+//   K3 k_gl_rows_out   each row of P: forward FFT (x 1/Mp), truncate to M, then either write
+//                      the right-hand side or apply one RK4 stage update (explicit RK4 of the
+//                      paper's time loop, or integrating-factor RK4) to the stage input V,
+//                      the accumulator A and the state S.
+// Explicit RK4 (a = 1/6, 1/3, 1/3, 1/6; b = 1/2, 1/2, 1), stage s with input V (V = S at s = 0):
+//     d = L V - N(V);  s < 3: V <- S + b_s dt d, A <- (s ? A : S) + a_s dt d;  s = 3: S <- A + a_3 dt d.
+// Integrating-factor RK4 (classical RK4 on exp(-L t) u_hat, E = exp(L dt / 2)), n = -N(V):
+//     s = 0: V <- E (S + dt/2 n),  A <- E^2 S + dt/6 E^2 n
+//     s = 1: V <- E S + dt/2 n,    A <- A + dt/3 E n
+//     s = 2: V <- E^2 S + dt E n,  A <- A + dt/3 E n
+//     s = 3: S <- A + dt/6 n
+#pragma once
+#include "k_fast.cuh"
+
+namespace sgm {
+
+enum GlMode { kGlRhs = 0, kGlRk4 = 1, kGlIfRk4 = 2 };
+
+struct GlParams {
+  double beta, gamma, dt, kscale;   // kscale = 2 pi / domain length
+  int stage;
+};
+
+// padded position of original index j of a length-M C2C axis, and the inverse map
+template <int M, int MP> __device__ __forceinline__ int gl_padpos(int j) { return j < (M + 1) / 2 ? j : j - M + MP; }
+template <int M, int MP> __device__ __forceinline__ int gl_origidx(int q) {
+  return q < (M + 1) / 2 ? q : (q >= MP - M / 2 ? q - MP + M : -1);
+}
+template <int M> __device__ __forceinline__ int gl_wavenumber(int j) { return j < (M + 1) / 2 ? j : j - M; }
+
+template <typename T> __host__ __device__ constexpr int gl_tw() { return 4; }
+
+template <typename T, int M, int MP>
+__global__ void __launch_bounds__(kFastThreads) k_gl_rows_pad(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ P,
+                                                              const cplx<T>* __restrict__ twf) {
+  using C = cplx<T>;
+  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  constexpr int LDP = pad_ld(MP);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int r0 = blockIdx.x * LINES;
+  const int nl = min(LINES, M - r0);
+  for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
+    const int line = idx / MP, q = idx - line * MP;
+    const int j = gl_origidx<M, MP>(q);
+    buf[line * LDP + padi(q)] = j >= 0 ? U[(long)(r0 + line) * M + j] : mk<C>((T)0, (T)0);
+  }
+  __syncthreads();
+  fft_fast<MP, LINES, kFastThreads, true>(buf, nl, twf);
+  for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
+    const int line = idx / MP, q = idx - line * MP;
+    P[(long)(r0 + line) * MP + q] = buf[line * LDP + padi(q)];
+  }
+}
+
+template <typename T, int M, int MP>
+__global__ void __launch_bounds__(kFastThreads) k_gl_cols(cplx<T>* __restrict__ P, const cplx<T>* __restrict__ twf,
+                                                          double gamma) {
+  using C = cplx<T>;
+  constexpr int TW = gl_tw<T>();
+  constexpr int LDP = pad_ld(MP);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int c0 = blockIdx.x * TW;
+  const int nt = min(TW, MP - c0);
+  for (int idx = threadIdx.x; idx < MP * TW; idx += kFastThreads) {
+    const int q = idx / TW, t = idx % TW;
+    if (t < nt) {
+      const int j = gl_origidx<M, MP>(q);
+      buf[t * LDP + padi(q)] = j >= 0 ? P[(long)j * MP + c0 + t] : mk<C>((T)0, (T)0);
+    }
+  }
+  __syncthreads();
+  fft_fast<MP, TW, kFastThreads, true>(buf, nt, twf);
+  const T g = (T)gamma;
+  for (int idx = threadIdx.x; idx < MP * TW; idx += kFastThreads) {
+    const int t = idx / MP, q = idx - t * MP;
+    if (t < nt) {
+      const C u = buf[t * LDP + padi(q)];
+      const T s2 = u.x * u.x + u.y * u.y;
+      buf[t * LDP + padi(q)] = mk<C>(s2 * (u.x - g * u.y), s2 * (u.y + g * u.x));   // (1 + i gamma)|u|^2 u
+    }
+  }
+  __syncthreads();
+  fft_fast<MP, TW, kFastThreads, false>(buf, nt, twf);
+  const T s = (T)1 / (T)MP;
+  for (int idx = threadIdx.x; idx < M * TW; idx += kFastThreads) {
+    const int j = idx / TW, t = idx % TW;
+    if (t < nt) P[(long)j * MP + c0 + t] = cscale(buf[t * LDP + padi(gl_padpos<M, MP>(j))], s);
+  }
+}
+
+template <typename T, int M, int MP, int MODE>
+__global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __restrict__ P, const cplx<T>* Vin,
+                                                              cplx<T>* Vout, cplx<T>* A, cplx<T>* S,
+                                                              const cplx<T>* __restrict__ E, cplx<T>* out,
+                                                              const __grid_constant__ GlParams prm,
+                                                              const cplx<T>* __restrict__ twf) {
+  using C = cplx<T>;
+  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  constexpr int LDP = pad_ld(MP);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int r0 = blockIdx.x * LINES;
+  const int nl = min(LINES, M - r0);
+  for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
+    const int line = idx / MP, q = idx - line * MP;
+    buf[line * LDP + padi(q)] = P[(long)(r0 + line) * MP + q];
+  }
+  __syncthreads();
+  fft_fast<MP, LINES, kFastThreads, false>(buf, nl, twf);
+  const T inv = (T)1 / (T)MP;
+  const T beta = (T)prm.beta, dt = (T)prm.dt, ks = (T)prm.kscale;
+  for (int idx = threadIdx.x; idx < nl * M; idx += kFastThreads) {
+    const int line = idx / M, j = idx - line * M;
+    const int r = r0 + line;
+    const long g = (long)r * M + j;
+    const C nl_ = cscale(buf[line * LDP + padi(gl_padpos<M, MP>(j))], inv);   // N(V) at (r, j)
+    if (MODE == kGlIfRk4) {
+      const C n = mk<C>(-nl_.x, -nl_.y);
+      const C e = E[g];
+      const C s = S[g];
+      switch (prm.stage) {
+        case 0: {
+          const C e2 = cmul(e, e);
+          Vout[g] = cmul(e, mk<C>(s.x + (T)0.5 * dt * n.x, s.y + (T)0.5 * dt * n.y));
+          const C t = cadd(s, cscale(n, dt / (T)6));
+          A[g] = cmul(e2, t);
+          break;
+        }
+        case 1: {
+          const C es = cmul(e, s);
+          Vout[g] = mk<C>(es.x + (T)0.5 * dt * n.x, es.y + (T)0.5 * dt * n.y);
+          const C en = cmul(e, n);
+          const C a = A[g];
+          A[g] = mk<C>(a.x + dt / (T)3 * en.x, a.y + dt / (T)3 * en.y);
+          break;
+        }
+        case 2: {
+          const C e2 = cmul(e, e);
+          const C en = cmul(e, n);
+          const C e2s = cmul(e2, s);
+          Vout[g] = mk<C>(e2s.x + dt * en.x, e2s.y + dt * en.y);
+          const C a = A[g];
+          A[g] = mk<C>(a.x + dt / (T)3 * en.x, a.y + dt / (T)3 * en.y);
+          break;
+        }
+        default: {
+          const C a = A[g];
+          S[g] = mk<C>(a.x + dt / (T)6 * n.x, a.y + dt / (T)6 * n.y);
+          break;
+        }
+      }
+    } else {
+      const T kx = ks * (T)gl_wavenumber<M>(r), ky = ks * (T)gl_wavenumber<M>(j);
+      const T k2 = kx * kx + ky * ky;
+      const C v = Vin[g];
+      // L v = (1 - k2) v - i beta k2 v
+      const C d = mk<C>((1 - k2) * v.x + beta * k2 * v.y - nl_.x, (1 - k2) * v.y - beta * k2 * v.x - nl_.y);
+      if (MODE == kGlRhs) {
+        out[g] = d;
+      } else {
+        const int st = prm.stage;
+        const T a_s = (st == 0 || st == 3) ? (T)1 / (T)6 : (T)1 / (T)3;
+        const T b_s = (st == 2) ? (T)1 : (T)0.5;
+        if (st < 3) {
+          const C s = S[g];
+          const C base = (st == 0) ? s : A[g];
+          A[g] = mk<C>(base.x + a_s * dt * d.x, base.y + a_s * dt * d.y);
+          Vout[g] = mk<C>(s.x + b_s * dt * d.x, s.y + b_s * dt * d.y);
+        } else {
+          const C a = A[g];
+          S[g] = mk<C>(a.x + a_s * dt * d.x, a.y + a_s * dt * d.y);
+        }
+      }
+    }
+  }
+}
+
+// ---- launch of one right-hand side evaluation + stage update --------------------------------
+template <typename T, int M, int MP>
+cudaError_t gl_launch_sized(int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E,
+                            cplx<T>* out, cplx<T>* P, const GlParams& prm, const cplx<T>* twf, cudaStream_t st) {
+  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  constexpr int TW = gl_tw<T>();
+  const size_t smem_rows = sizeof(cplx<T>) * LINES * pad_ld(MP);
+  const size_t smem_cols = sizeof(cplx<T>) * TW * pad_ld(MP);
+  cudaError_t e;
+  if ((e = fast_smem(k_gl_rows_pad<T, M, MP>, smem_rows)) != cudaSuccess) return e;
+  if ((e = fast_smem(k_gl_cols<T, M, MP>, smem_cols)) != cudaSuccess) return e;
+  const unsigned grows = (M + LINES - 1) / LINES;
+  k_gl_rows_pad<T, M, MP><<<grows, kFastThreads, smem_rows, st>>>(Vin, P, twf);
+  k_gl_cols<T, M, MP><<<(MP + TW - 1) / TW, kFastThreads, smem_cols, st>>>(P, twf, prm.gamma);
+  switch (mode) {
+    case kGlRhs:
+      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlRhs>, smem_rows)) != cudaSuccess) return e;
+      k_gl_rows_out<T, M, MP, kGlRhs><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      break;
+    case kGlRk4:
+      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlRk4>, smem_rows)) != cudaSuccess) return e;
+      k_gl_rows_out<T, M, MP, kGlRk4><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      break;
+    default:
+      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlIfRk4>, smem_rows)) != cudaSuccess) return e;
+      k_gl_rows_out<T, M, MP, kGlIfRk4><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gl_launch(int M, int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E,
+                      cplx<T>* out, cplx<T>* P, const GlParams& prm, const cplx<T>* twf, cudaStream_t st) {
+  switch (M) {
+#define SGM_GL(m) case m: return gl_launch_sized<T, m, 3 * m / 2>(mode, Vin, Vout, A, S, E, out, P, prm, twf, st);
+    SGM_GL(32) SGM_GL(64) SGM_GL(128) SGM_GL(256) SGM_GL(512) SGM_GL(1024)
+#undef SGM_GL
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace sgm

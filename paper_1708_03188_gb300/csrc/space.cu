@@ -18,9 +18,8 @@
 #include <string>
 #include <vector>
 
-#include "../../include/sgm.h"
-#include "common.cuh"
 #include "fft_fast.cuh"
+#include "space_internal.cuh"
 
 using namespace sgm;
 
@@ -80,33 +79,6 @@ int sgm::set_error(int code, const char* fmt, ...) {
   return code;
 }
 
-struct sgm_space {
-  static constexpr uint32_t kMagic = 0x5347'4d53u;
-  uint32_t magic = kMagic;
-  int device = 0;
-  int ndim = 0;
-  int kinds[3] = {0, 0, 0};
-  int64_t n[3] = {1, 1, 1};
-  double dom[6] = {0, 0, 0, 0, 0, 0};
-  int prec = SGM_F64;
-  bool cheb = false;       // axis 0 is a Chebyshev axis
-  bool real_phys = false;  // physical array is real
-  bool real_spec = false;  // spectral array is real (1-D Chebyshev)
-  int64_t spec[3] = {1, 1, 1};
-  long nphys = 0, nspec = 0;
-  size_t phys_bytes = 0, spec_bytes = 0;
-  std::map<int, void*> tw;   // length -> exp(-2 pi i k / L)
-  std::map<int, void*> twf;  // length -> pass twiddle tables of the compile-time FFT engine
-  void* dctw = nullptr;      // exp(-i pi k / (2N))
-  double* tab = nullptr;     // Galerkin coefficient tables (Dirichlet or biharmonic)
-  void* W1 = nullptr;
-  void* W2 = nullptr;
-  double* scratch = nullptr;
-  long scratch_threads = 0;
-
-  size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
-  size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
-};
 
 namespace {
 
@@ -145,8 +117,14 @@ template <typename T> int upload_fast_twiddles(int L, void** out) {
   return SGM_OK;
 }
 
+}  // namespace
+
+int sgm::make_fast_twiddles(int precision, int L, void** out) {
+  return precision == SGM_F32 ? upload_fast_twiddles<float>(L, out) : upload_fast_twiddles<double>(L, out);
+}
+
 // pass tables for the compile-time engine when L has a compiled kernel (else nullptr)
-int need_twf(sgm_space* s, int L, const void** out) {
+int sgm::need_twf(sgm_space* s, int L, const void** out) {
   *out = nullptr;
   if (!fast_compiled(L)) return SGM_OK;
   if (!s->twf.count(L)) {
@@ -158,6 +136,8 @@ int need_twf(sgm_space* s, int L, const void** out) {
   *out = s->twf[L];
   return SGM_OK;
 }
+
+namespace {
 
 template <typename T> int upload_dctw(sgm_space* s, int N) {
   std::vector<cplx<T>> h(N);
@@ -438,6 +418,12 @@ template <typename T> int backward_impl(sgm_space* s, const void* uh, void* u, c
   SGM_TRY(cheb_pass<T>(s, kChebBackward, uh, s->W1, st, wide));
   return fourier_backward<T>(s, s->W1, u, st);
 }
+
+}  // namespace
+
+int sgm::space_check(const sgm_space* s) { return check_space(s); }
+
+namespace {
 
 void free_space(sgm_space* s) {
   for (auto& kv : s->tw) cudaFree(kv.second);

@@ -1,0 +1,45 @@
+// space_internal.cuh - the sgm_space object shared by the host translation units
+// (space.cu, gl.cu).
+#pragma once
+#include <map>
+#include <stdint.h>
+
+#include "../../include/sgm.h"
+#include "common.cuh"
+
+struct sgm_space {
+  static constexpr uint32_t kMagic = 0x5347'4d53u;
+  uint32_t magic = kMagic;
+  int device = 0;
+  int ndim = 0;
+  int kinds[3] = {0, 0, 0};
+  int64_t n[3] = {1, 1, 1};
+  double dom[6] = {0, 0, 0, 0, 0, 0};
+  int prec = SGM_F64;
+  bool cheb = false;       // axis 0 is a Chebyshev axis
+  bool real_phys = false;  // physical array is real
+  bool real_spec = false;  // spectral array is real (1-D Chebyshev)
+  int64_t spec[3] = {1, 1, 1};
+  long nphys = 0, nspec = 0;
+  size_t phys_bytes = 0, spec_bytes = 0;
+  std::map<int, void*> tw;   // length -> exp(-2 pi i k / L)
+  std::map<int, void*> twf;  // length -> pass twiddle tables of the compile-time FFT engine
+  void* dctw = nullptr;      // exp(-i pi k / (2N))
+  double* tab = nullptr;     // Galerkin coefficient tables (Dirichlet or biharmonic)
+  void* W1 = nullptr;
+  void* W2 = nullptr;
+  double* scratch = nullptr;
+  long scratch_threads = 0;
+
+  size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
+  size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
+};
+
+namespace sgm {
+// pass tables of the compile-time FFT engine for length L on this space's device and
+// precision (nullptr if L has no compiled kernel); owned by the space
+int need_twf(sgm_space* s, int L, const void** out);
+int space_check(const sgm_space* s);
+// device table of the compile-time FFT engine for length L (caller frees)
+int make_fast_twiddles(int precision, int L, void** out);
+}  // namespace sgm

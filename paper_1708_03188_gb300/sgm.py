@@ -32,6 +32,10 @@ _SIGNATURES = {
     "sgm_biharmonic_solve": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
     "sgm_helmholtz": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
     "sgm_biharmonic": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
+    "sgm_gl_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _D, _D, _D, _D, ctypes.c_int]),
+    "sgm_gl_destroy": (ctypes.c_int, [_VP]),
+    "sgm_gl_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_gl_step": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
     "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int,
                                                    _D, _D, _VP, _VP, _VP]),
@@ -166,3 +170,46 @@ class Space:
 
     def biharmonic(self, a, b, c, f, out=None, stream=None):
         return self._run(lib().sgm_biharmonic, f, False, False, out, stream, a, b, c)
+
+
+GL_SCHEMES = {"rk4": 0, "ifrk4": 1}
+
+
+class GinzburgLandau:
+    """Stepper for u_t = u + (1 + i beta) lap(u) - (1 + i gamma)|u|^2 u (include/sgm.h, sgm_gl_*).
+
+    space: a square C2C x C2C Space (e.g. domain [(-50, 50), (-50, 50)]); scheme "rk4" (the
+    paper's explicit RK4) or "ifrk4" (integrating-factor RK4); padding must be 1.5.
+    """
+
+    def __init__(self, space, beta, gamma, dt, scheme="rk4", padding=1.5):
+        self.space = space
+        self.shape = space.spectral_shape
+        self.dtype = space.spectral_dtype
+        self._h = _VP()
+        check(lib().sgm_gl_create(ctypes.byref(self._h), space._h, float(padding), float(beta), float(gamma),
+                                  float(dt), GL_SCHEMES[scheme]))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sgm_gl_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def rhs(self, u_hat, out=None, stream=None):
+        self.space._check(u_hat, self.shape, self.dtype, "u_hat")
+        out = torch.empty_like(u_hat) if out is None else out
+        self.space._check(out, self.shape, self.dtype, "out")
+        check(lib().sgm_gl_rhs(self._h, _ptr(u_hat), _ptr(out), _stream(stream)))
+        return out
+
+    def step(self, u_hat, nsteps=1, stream=None):
+        """Advance u_hat in place by nsteps steps."""
+        self.space._check(u_hat, self.shape, self.dtype, "u_hat")
+        check(lib().sgm_gl_step(self._h, _ptr(u_hat), int(nsteps), _stream(stream)))
+        return u_hat
