@@ -37,7 +37,7 @@ METRIC = "Gdof/s transform+solve (3-D Poisson + biharmonic, Cheb 256 x Fourier 2
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--precision", choices=["f32", "f64"], default="f32")
@@ -56,6 +56,18 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(value, device="cpu"):
+    """Largest value over the ranks of the default process group (the value itself when
+    torch.distributed is not initialised)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def manufactured(kinds):
     from paper_1708_03188_gb300 import inputs
     x, y, z = inputs.mesh(kinds, (N0, N1, N2))
@@ -68,7 +80,7 @@ def manufactured(kinds):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -82,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
         time.sleep(0.3)
@@ -140,10 +152,12 @@ def hbm_peak():
 
 
 # FP64 operations (an FMA counts 2) per Chebyshev row per complex Fourier column in the
-# eliminations of k_solve.cu: Dirichlet 28, biharmonic 62 (assembly of the row from the
-# coefficient tables, elimination of the sub-diagonal entries with their right-hand
-# sides, one reciprocal counted as 1, back substitution with the running tail sums).
-FLOPS_PER_ROW = {"dirichlet": 28, "biharmonic": 62}
+# eliminations of k_solve.cu, where the columns +m and -m share one factorisation:
+#   Dirichlet  (15 per row of the shared factorisation) / 2 + 16 per right-hand-side column = 23.5
+#   biharmonic (53 per row of the shared factorisation) / 2 + 34 per right-hand-side column = 60.5
+# (row assembly from the coefficient tables, elimination of the sub-diagonal entries, one
+# reciprocal = approximation + cubic Newton step, back substitution with the tail sums).
+FLOPS_PER_ROW = {"dirichlet": 23.5, "biharmonic": 60.5}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
 
 
@@ -212,11 +226,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, "cuda")
     err_p = float(torch.linalg.vector_norm((u_p.double().cpu() - torch.from_numpy(np.ascontiguousarray(uP_exact))))
                   / np.linalg.norm(uP_exact))
     err_b = float(torch.linalg.vector_norm((u_b.double().cpu() - torch.from_numpy(np.ascontiguousarray(uB_exact))))
@@ -295,11 +305,7 @@ def run_ours(args):
         e2e_step()
     b.record(stream)
     b.synchronize()
-    e2e_ms = a.elapsed_time(b) / e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, "cuda")
 
     gl = gl_measure(Space, stream, steps=args.gl_steps) if args.gl_steps > 0 else None
 

@@ -63,7 +63,7 @@ extern "C" {
 #define SGM_ERR_ALLOC -7       /* device or host allocation failed */
 #define SGM_ERR_STATE -8       /* object used after destroy or with a mismatched kind */
 
-/* basis kinds (Sec. 3.2 of the paper, the bases of shenfun.chebyshev and shenfun.fourier) */
+/* basis kinds (Sec. 3.1 of the paper, the bases of shenfun.chebyshev and shenfun.fourier) */
 #define SGM_CHEBYSHEV 0          /* regular T_k, k = 0..N-1 */
 #define SGM_SHEN_DIRICHLET 1     /* T_k - T_{k+2}, k = 0..N-3 (Eq. chebdirichlet) */
 #define SGM_SHEN_BIHARMONIC 2    /* T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4}, k = 0..N-5 (Eq. chebbiharmonic) */
@@ -86,7 +86,7 @@ const char* sgm_last_error(void);
 const char* sgm_status_string(int status);
 
 /*
- * Create a tensor-product space (the TensorProductSpace of Sec. 4; bases of Sec. 3.2).
+ * Create a tensor-product space (the TensorProductSpace of Sec. 4; bases of Sec. 3.1).
  *   out        receives the new space.
  *   ndim       1..3.
  *   kinds      ndim basis kinds (see above).
