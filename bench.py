@@ -308,6 +308,7 @@ def run_ours(args):
     e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, "cuda")
 
     gl = gl_measure(Space, stream, steps=args.gl_steps) if args.gl_steps > 0 else None
+    batch = batch_measure(stream)
 
     value = world * DOF_PER_STEP / (ms * 1e-3) / 1e9
     line = None
@@ -333,6 +334,7 @@ def run_ours(args):
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
             "gl": gl,
+            "batch": batch,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -369,6 +371,35 @@ def gl_measure(Space, stream, M=512, steps=200):
                                               "finite_after": finite, "launches_per_step": 12}
             gl.close()
         sp.close()
+    return out
+
+
+def batch_measure(stream, reps=20):
+    """4096 independent 1-D Dirichlet Helmholtz problems u'' - alpha u = f (sizes log-uniform in
+    [16, 2048], alpha ~ U(0, 1e4), seeded), one sgm_batch_helmholtz call (3 launches) per batch."""
+    import torch
+    from paper_1708_03188_gb300 import inputs
+    from paper_1708_03188_gb300.sgm import Batch1D
+    sizes, alpha, fs = inputs.batch1d(4096)
+    out = {"problems": 4096, "dof": int(sizes.sum()), "N_range": [int(sizes.min()), int(sizes.max())]}
+    for prec in ("f32", "f64"):
+        b = Batch1D(sizes, alpha, prec)
+        f = torch.from_numpy(np.concatenate(fs)).to(b.dtype).cuda()
+        u = torch.empty_like(f)
+        for _ in range(3):
+            b.solve(f, out=u)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            b.solve(f, out=u)
+        e.record(stream)
+        e.synchronize()
+        ms = a.elapsed_time(e) / reps
+        out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round(int(sizes.sum()) / (ms * 1e-3) / 1e9, 4),
+                     "launches_per_batch": 3}
+        b.close()
     return out
 
 

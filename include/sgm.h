@@ -188,6 +188,29 @@ int sgm_gl_rhs(sgm_gl* gl, const void* u_hat, void* rhs, void* stream);
 /* Advance u_hat (in place) by nsteps time steps of the stepper's scheme. */
 int sgm_gl_step(sgm_gl* gl, void* u_hat, int nsteps, void* stream);
 
+/* ---- batched independent 1-D Helmholtz problems ------------------------------------------- */
+typedef struct sgm_batch sgm_batch;
+
+/*
+ * Describe a batch of nprob independent problems  u_p'' - alpha_p u_p = f_p  on [-1, 1] with
+ * u_p(+-1) = 0, problem p on its own Chebyshev-Gauss grid of n[p] points (4 <= n[p] <= 4096),
+ * discretised with the Shen-Dirichlet basis (Sec. 3.4.2; the weak form of sgm_helmholtz_solve
+ * with a = 1, b = -alpha_p, kappa = 0).  precision SGM_F32 (FP32 transforms, FP64
+ * eliminations) or SGM_F64.  Builds the size-sorted problem table, per-size FFT plans and
+ * twiddles and the FP64 work buffers on the current device.
+ */
+int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double* alpha, int precision);
+int sgm_batch_destroy(sgm_batch* batch);
+/* Element offsets of the problems in the packed arrays: offsets[p] = n[0] + ... + n[p-1], nprob+1 entries. */
+int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets);
+/*
+ * Solve every problem: f and u are packed real arrays (float or double) of sum(n) values,
+ * problem p at offsets[p] (the samples at x_j = cos((2j+1) pi / (2 n[p])).  Three kernel
+ * launches on `stream`: DCT-II + stencil per problem, the FP64 eliminations (32 problems per
+ * warp), stencil + DCT-III per problem.  f and u must not overlap.
+ */
+int sgm_batch_helmholtz(sgm_batch* batch, const void* f, void* u, void* stream);
+
 /*
  * Dirichlet Helmholtz solve that allocates nothing (no counterpart in the paper; it is an
  * interface choice of this library).

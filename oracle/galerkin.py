@@ -17,20 +17,40 @@ forms of
 after dividing both sides by the common Fourier factor (2 pi per periodic axis,
 or its domain length), are solved here by dense LU.
 """
+import functools
+
 import numpy as np
 
 from . import quadrature
 
 
-def matrices(kind, N):
-    """Dense B, A, S for the basis ``kind`` with N quadrature points."""
+@functools.lru_cache(maxsize=32)
+def _matrix(kind, N, q):
+    """[m, l] = sum_j phi_m(x_j) w_j phi_l^(q)(x_j), the quadrature of (phi_l^(q), phi_m)_w^N."""
     x, w = quadrature.gauss_points(N)
     phi = quadrature.basis_values(kind, N, x, 0)          # (N, nb)
-    out = {}
-    for name, q in (("B", 0), ("A", 2), ("S", 4)):
-        dphi = quadrature.basis_values(kind, N, x, q)
-        out[name] = (phi * w[:, None]).T @ dphi             # [m, l] = sum_j phi_m(x_j) w_j phi_l^(q)(x_j)
-    return out
+    dphi = quadrature.basis_values(kind, N, x, q)
+    m = (phi * w[:, None]).T @ dphi
+    m.setflags(write=False)
+    return m
+
+
+class _Matrices(dict):
+    """B, A, S computed on first access (each an independent quadrature)."""
+
+    def __init__(self, kind, N):
+        super().__init__()
+        self.kind, self.N = kind, N
+
+    def __missing__(self, name):
+        value = _matrix(self.kind, self.N, {"B": 0, "A": 2, "S": 4}[name])
+        self[name] = value
+        return value
+
+
+def matrices(kind, N):
+    """Dense B, A, S for the basis ``kind`` with N quadrature points (computed when first used)."""
+    return _Matrices(kind, N)
 
 
 def helmholtz_matrix(mats, a, b, kappa2):

@@ -43,9 +43,15 @@ def basis_coefficients(kind, N):
 
 
 def basis_values(kind, N, x, deriv=0):
-    """V[j, l] = d^deriv phi_l / dx^deriv evaluated at x_j."""
+    """V[j, l] = d^deriv phi_l / dx^deriv evaluated at x_j.
+
+    The T-coefficients of phi_l (differentiated in coefficient space) are summed against
+    the Chebyshev Vandermonde matrix T_k(x_j) (three-term recurrence).
+    """
     P = basis_coefficients(kind, N)
     coef = P.T                                   # (N, nb): one series per column
     if deriv:
         coef = npcheb.chebder(coef, m=deriv, axis=0)
-    return npcheb.chebval(np.asarray(x, dtype=np.float64), coef, tensor=True).T
+    x = np.asarray(x, dtype=np.float64)
+    V = npcheb.chebvander(x, coef.shape[0] - 1)  # (len(x), deg+1)
+    return V @ coef

@@ -69,6 +69,8 @@ __device__ __forceinline__ double kappa2_of(const Wavenumbers& w, long c) {
 
 // ---- error reporting (space.cu): sets the thread-local message of sgm_last_error ---------
 int set_error(int code, const char* fmt, ...);
+// radix sequence of the runtime engine for length L (space.cu)
+FftPlan host_plan(int L);
 
 // ---- launchers (defined in k_fourier.cu, k_cheb.cu, k_solve.cu) --------------------------
 // All return cudaGetLastError() after the launch.

@@ -1,0 +1,188 @@
+// k_batch.cu - batched independent 1-D Shen-Dirichlet Helmholtz problems
+//     u_p'' - alpha_p u_p = f_p  on [-1, 1], u_p(+-1) = 0,   p = 0..P-1,
+// each with its own number of Chebyshev-Gauss points N_p (any 4 <= N_p <= 4096), transform +
+// solve + transform (the weak form of Sec. 3.4.2 with a = 1, b = -alpha_p, kappa = 0).
+//
+// Work decomposition for GB300, where an FP64 warp-instruction occupies its sub-partition's
+// FP64 pipe for ~64 cycles whatever the number of active lanes:
+//   K_A  one CTA per problem: DCT-II of the real samples via one complex FFT (runtime-radix
+//        engine, any N), Dirichlet stencil S_k = t_k - t_{k+2}; S_k is written in FP64 into a
+//        warp-interleaved layout [warp][row][lane] (problems sorted by N, 32 per warp).
+//   K_B  one thread per (problem, parity): the FP64 elimination of k_solve.cu's Dirichlet
+//        kernel with kappa = 0, lanes = 32 problems of similar size, so every FP64 instruction
+//        serves 32 problems and every load/store of a row is one 256-byte access.
+//   K_C  one CTA per problem: stencil a_k = u_k - u_{k-2} and DCT-III back to the points.
+#include <algorithm>
+
+#include "convert.cuh"
+#include "fft_core.cuh"
+
+namespace sgm {
+
+struct BatchProblem {
+  int N;          // Chebyshev points
+  int slot;       // position in the size-sorted order: warp = slot / 32, lane = slot % 32
+  long offset;    // first element of f_p / u_p in the caller's arrays
+  double alpha;
+  int tw_off;     // exp(-2 pi i k / N), k < N, in the twiddle pool
+  int dct_off;    // exp(-i pi k / (2N)), k < N, in the twiddle pool
+  int plan;       // index into the plan table
+};
+
+// interleaved FP64 arrays: element (row k, slot s) at wbase[s / 32] + k * 32 + s % 32
+__device__ __forceinline__ long ilv(const long* wbase, int slot, int k) {
+  return wbase[slot >> 5] + (long)k * 32 + (slot & 31);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_dct(const T* __restrict__ f, const BatchProblem* __restrict__ probs,
+                                                   const int* __restrict__ by_slot, const FftPlan* __restrict__ plans,
+                                                   const cplx<T>* __restrict__ pool, const long* __restrict__ wbase,
+                                                   double* __restrict__ S, int Nmax) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchProblem pr = probs[by_slot[blockIdx.x]];   // largest problems first
+  const int N = pr.N;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + (Nmax + 1);
+  for (int j = threadIdx.x; j < N; j += blockDim.x)
+    A[(j & 1) ? N - 1 - (j >> 1) : (j >> 1)] = mk<C>(f[pr.offset + j], (T)0);
+  __syncthreads();
+  const FftPlan plan = plans[pr.plan];
+  C* V = fft_lines<false>(A, B, 1, Nmax + 1, plan, pool + pr.tw_off);
+  C* M = (V == A) ? B : A;
+  const C* dctw = pool + pr.dct_off;
+  const T scale = (T)3.14159265358979323846 / (T)N;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const C v = V[k], vr = cconj(V[k == 0 ? 0 : N - k]);
+    const C w = __ldg(&dctw[k]);
+    const C a = cadd(v, vr);
+    M[k] = mk<C>((T)0.5 * scale * (w.x * a.x - w.y * a.y), (T)0);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    S[ilv(wbase, pr.slot, k)] = k < N - 2 ? widen<T>(M[k].x - M[k + 2].x) : 0.0;
+}
+
+__device__ __forceinline__ double rcp64b(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
+}
+
+// thread = (slot, parity); U (interleaved) receives the Shen coefficients
+__global__ void __launch_bounds__(128) k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ by_slot,
+                                                     const long* __restrict__ wbase, const double* __restrict__ S,
+                                                     double* __restrict__ U, double* __restrict__ scratch,
+                                                     const long* __restrict__ sbase, int nslots) {
+  const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // global warp
+  const int lane = threadIdx.x & 31;
+  const int wslot = w >> 1;          // slot warp
+  const int p = w & 1;               // parity
+  const int slot = wslot * 32 + lane;
+  if (slot >= nslots) return;
+  const BatchProblem pr = probs[by_slot[slot]];
+  const int N = pr.N, nb = N - 2;
+  const double pi = 3.141592653589793;
+  const double aB = -pr.alpha;       // a = 1, b = -alpha, kappa = 0
+  const double ell = -aB * 0.5 * pi;
+  const int n = (nb - p + 1) / 2;
+  const long rbase = wbase[wslot] + lane;
+  double* s = scratch + sbase[wslot] * 2 + (long)p * (sbase[wslot + 1] - sbase[wslot]) + lane;
+  double pr_ = 0.0, pg = 0.0, pge = 0.0, pf = 0.0;
+  double fn = n > 0 ? S[rbase + (long)p * 32] : 0.0;
+  for (int i = 0; i < n; ++i) {
+    const int k = p + 2 * i;
+    double f = fn;
+    if (i + 1 < n) fn = S[rbase + (long)(k + 2) * 32];
+    const double kp1 = (double)(k + 1);
+    double d = -2.0 * pi * kp1 * (kp1 + 1.0) + aB * (k == 0 ? 1.5 * pi : pi);
+    double g = -4.0 * pi * kp1;
+    if (i > 0) {
+      const double mu = ell * pr_;
+      d = fma(-mu, pge, d);
+      g = fma(-mu, pg, g);
+      f = fma(-mu, pf, f);
+    }
+    const double r = rcp64b(d);
+    s[0] = r;
+    s[32] = g;
+    s[64] = f;
+    s += 96;
+    pr_ = r; pg = g; pge = g + ell; pf = f;
+  }
+  double un = 0.0, Ts = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    const int k = p + 2 * i;
+    s -= 96;
+    const double r = s[0], g = s[32], f = s[64];
+    Ts += un;
+    const double u = fma(-g, Ts, fma(-ell, un, f)) * r;
+    U[rbase + (long)k * 32] = u;
+    un = u;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_idct(T* __restrict__ u, const BatchProblem* __restrict__ probs,
+                                                    const int* __restrict__ by_slot, const FftPlan* __restrict__ plans,
+                                                    const cplx<T>* __restrict__ pool, const long* __restrict__ wbase,
+                                                    const double* __restrict__ U, int Nmax) {
+  using C = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const BatchProblem pr = probs[by_slot[blockIdx.x]];   // largest problems first
+  const int N = pr.N, nb = N - 2;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + (Nmax + 1);
+  for (int k = threadIdx.x; k < N; k += blockDim.x)
+    B[k] = mk<C>(k < nb ? narrow<T>(U[ilv(wbase, pr.slot, k)]) : (T)0, (T)0);
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += blockDim.x) A[k] = k >= 2 ? csub(B[k], B[k - 2]) : B[k];
+  __syncthreads();
+  const C* dctw = pool + pr.dct_off;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    C v;
+    if (k == 0) {
+      v = A[0];
+    } else {
+      const C x = A[k], y = A[N - k];
+      v = cscale(cmulc(mk<C>(x.x + y.y, x.y - y.x), __ldg(&dctw[k])), (T)0.5);
+    }
+    B[k] = v;
+  }
+  __syncthreads();
+  const FftPlan plan = plans[pr.plan];
+  C* R = fft_lines<true>(B, A, 1, Nmax + 1, plan, pool + pr.tw_off);
+  for (int j = threadIdx.x; j < N; j += blockDim.x) u[pr.offset + j] = R[(j & 1) ? N - 1 - (j >> 1) : (j >> 1)].x;
+}
+
+template <typename T>
+cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int Nmax, const void* probs,
+                         const int* by_slot, const void* plans, const void* pool, const long* wbase, double* S,
+                         double* U, double* scratch, const long* sbase, cudaStream_t s) {
+  if (nprob <= 0) return cudaSuccess;
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)(Nmax + 1);
+  cudaError_t e;
+  if (smem > 48 * 1024) {
+    if ((e = cudaFuncSetAttribute(k_batch_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_batch_idct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+  }
+  const BatchProblem* P = (const BatchProblem*)probs;
+  k_batch_dct<T><<<nprob, 256, smem, s>>>((const T*)f, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, S,
+                                          Nmax);
+  const int warps = 2 * ((nslots + 31) / 32);
+  k_batch_solve<<<(warps + 3) / 4, 128, 0, s>>>(P, by_slot, wbase, S, U, scratch, sbase, nslots);
+  k_batch_idct<T><<<nprob, 256, smem, s>>>((T*)u, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, U,
+                                           Nmax);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_batch<float>(const void*, void*, int, int, int, const void*, const int*, const void*,
+                                         const void*, const long*, double*, double*, double*, const long*, cudaStream_t);
+template cudaError_t launch_batch<double>(const void*, void*, int, int, int, const void*, const int*, const void*,
+                                          const void*, const long*, double*, double*, double*, const long*, cudaStream_t);
+
+size_t batch_problem_bytes() { return sizeof(BatchProblem); }
+
+}  // namespace sgm

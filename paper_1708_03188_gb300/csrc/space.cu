@@ -69,6 +69,8 @@ FftPlan make_plan(int L) {
 
 }  // namespace
 
+FftPlan sgm::host_plan(int L) { return make_plan(L); }
+
 int sgm::set_error(int code, const char* fmt, ...) {
   char buf[512];
   va_list ap;

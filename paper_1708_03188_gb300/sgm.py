@@ -36,6 +36,11 @@ _SIGNATURES = {
     "sgm_gl_destroy": (ctypes.c_int, [_VP]),
     "sgm_gl_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sgm_gl_step": (ctypes.c_int, [_VP, _VP, ctypes.c_int, _VP]),
+    "sgm_batch_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.POINTER(_D), ctypes.c_int]),
+    "sgm_batch_destroy": (ctypes.c_int, [_VP]),
+    "sgm_batch_offsets": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "sgm_batch_helmholtz": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int,
                                                    _D, _D, _VP, _VP, _VP]),
@@ -213,3 +218,43 @@ class GinzburgLandau:
         self.space._check(u_hat, self.shape, self.dtype, "u_hat")
         check(lib().sgm_gl_step(self._h, _ptr(u_hat), int(nsteps), _stream(stream)))
         return u_hat
+
+
+class Batch1D:
+    """Batched independent problems u_p'' - alpha_p u_p = f_p, Shen-Dirichlet basis, one grid per
+    problem (sgm_batch_*).  f and u are packed 1-D tensors; problem p occupies offsets[p]:offsets[p+1]."""
+
+    def __init__(self, sizes, alpha, precision="f32"):
+        self.sizes = [int(v) for v in sizes]
+        self.precision = precision
+        nprob = len(self.sizes)
+        n = (ctypes.c_int64 * nprob)(*self.sizes)
+        a = (_D * nprob)(*[float(v) for v in alpha])
+        self._h = _VP()
+        check(lib().sgm_batch_create(ctypes.byref(self._h), nprob, n, a, PRECISION[precision]))
+        off = (ctypes.c_int64 * (nprob + 1))()
+        check(lib().sgm_batch_offsets(self._h, off))
+        self.offsets = [int(v) for v in off]
+        self.dtype = torch.float32 if precision == "f32" else torch.float64
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().sgm_batch_destroy(self._h)
+            self._h = _VP()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, f, out=None, stream=None):
+        total = self.offsets[-1]
+        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == self.dtype and f.numel() == total
+                and f.is_contiguous()):
+            raise ValueError(f"f must be a contiguous CUDA {self.dtype} tensor of {total} values")
+        out = torch.empty_like(f) if out is None else out
+        if not (out.is_cuda and out.dtype == self.dtype and out.numel() == total and out.is_contiguous()):
+            raise ValueError("bad output tensor")
+        check(lib().sgm_batch_helmholtz(self._h, _ptr(f), _ptr(out), _stream(stream)))
+        return out

@@ -1,0 +1,110 @@
+"""GPU parity of the batched 1-D Helmholtz problems against the FP64 oracle, problem by problem.
+
+Tolerances (relative L2 per problem): f64 max(1e-12, 32 * 2^-53 * cond(M_p)); f32 (FP32
+transforms, FP64 elimination) 2e-5.  The workload sizes are log-uniform in [16, 2048]; the
+small case spans several warps of 32 problems with a ragged last warp, prime sizes and the
+smallest N.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import galerkin
+from oracle.space import Space as OSpace
+from paper_1708_03188_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1708_03188_gb300 import build
+    build.build()
+
+
+def oracle_solve(N, alpha, f):
+    sp = OSpace(["dirichlet"], [N])
+    return sp.backward(sp.helmholtz(1.0, -alpha, sp.scalar_product(f)))
+
+
+def run(sizes, alpha, fs, prec):
+    from paper_1708_03188_gb300.sgm import Batch1D
+    b = Batch1D(sizes, alpha, prec)
+    dt = torch.float32 if prec == "f32" else torch.float64
+    f = torch.from_numpy(np.concatenate(fs)).to(dt).cuda()
+    u = b.solve(f).cpu().double().numpy()
+    fw = f.cpu().double().numpy()
+    return b, u, fw
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_mixed_sizes(prec):
+    g = np.random.default_rng(7)
+    sizes = [16, 17, 4, 5, 31, 64, 97, 128, 200, 256, 211, 13, 40, 6] * 3 + [512, 1021, 768, 2048]
+    alpha = g.uniform(0, 1e4, len(sizes))
+    alpha[:3] = 0.0                              # pure Poisson problems too
+    fs = [np.polynomial.chebyshev.chebval(inputs.cheb_points(N), g.standard_normal(N) * np.exp(-8.0 * np.arange(N) / N))
+          for N in sizes]
+    b, u, fw = run(sizes, alpha, fs, prec)
+    for p, N in enumerate(sizes):
+        o0, o1 = b.offsets[p], b.offsets[p + 1]
+        ref = oracle_solve(N, alpha[p], fw[o0:o1])
+        err = np.linalg.norm(u[o0:o1] - ref) / max(np.linalg.norm(ref), 1e-300)
+        if prec == "f64":
+            mats = galerkin.matrices("dirichlet", N)
+            cond = np.linalg.cond(galerkin.helmholtz_matrix(mats, 1.0, -alpha[p], 0.0))
+            tol = max(1e-12, 32 * EPS * cond)
+        else:
+            tol = 2e-5
+        assert err < tol, (p, N, alpha[p], err)
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-11), ("f32", 2e-5)])
+def test_largest_sizes_manufactured(prec, tol):
+    # u = (1 - x^2) exp(x) sin(3x): f = u'' - alpha u in closed form, at the largest sizes
+    def exact(x):
+        return (1 - x * x) * np.exp(x) * np.sin(3 * x)
+
+    def second(x):
+        e, s3, c3 = np.exp(x), np.sin(3 * x), np.cos(3 * x)
+        g, g1, g2 = 1 - x * x, -2 * x, -2.0
+        h, h1, h2 = e * s3, e * (s3 + 3 * c3), e * (-8 * s3 + 6 * c3)
+        return g2 * h + 2 * g1 * h1 + g * h2
+
+    sizes = [2048, 2044, 1500, 1999]
+    alpha = [0.0, 1e4, 37.5, 5e3]
+    fs = [second(inputs.cheb_points(N)) - a * exact(inputs.cheb_points(N)) for N, a in zip(sizes, alpha)]
+    b, u, _ = run(sizes, alpha, fs, prec)
+    for p, N in enumerate(sizes):
+        ue = exact(inputs.cheb_points(N))
+        err = np.linalg.norm(u[b.offsets[p]:b.offsets[p + 1]] - ue) / np.linalg.norm(ue)
+        assert err < tol, (N, err)
+
+
+def test_workload_sample_f32():
+    # the 4096-problem workload; 20 sampled problems plus the largest and the smallest
+    # compared one by one with the oracle
+    sizes, alpha, fs = inputs.batch1d(4096)
+    b, u, fw = run(sizes, alpha, fs, "f32")
+    g = np.random.default_rng(3)
+    pick = list(g.choice(len(sizes), 20, replace=False)) + [int(np.argmax(sizes)), int(np.argmin(sizes))]
+    for p in pick:
+        o0, o1 = b.offsets[p], b.offsets[p + 1]
+        ref = oracle_solve(int(sizes[p]), alpha[p], fw[o0:o1])
+        assert np.linalg.norm(u[o0:o1] - ref) / np.linalg.norm(ref) < 2e-5, p
+    assert np.all(np.isfinite(u))
+
+
+def test_errors():
+    from paper_1708_03188_gb300.sgm import Batch1D, SgmError
+    with pytest.raises(SgmError):
+        Batch1D([3, 16], [1.0, 1.0])
+    with pytest.raises(SgmError):
+        Batch1D([16], [float("nan")])
+    b = Batch1D([16, 20], [1.0, 2.0])
+    f = torch.zeros(36, device="cuda")
+    with pytest.raises(SgmError):
+        b.solve(f, out=f)
