@@ -211,6 +211,40 @@ int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets);
  */
 int sgm_batch_helmholtz(sgm_batch* batch, const void* f, void* u, void* stream);
 
+/* ---- learned closure kernels (no counterpart in the paper) -----------------------------------
+ * A periodic 3x3 convolution layer is the circular cross-correlation
+ *   y[b,o,i,j] = bias[o] + sum_{c,p,q} W[o,c,p,q] x[b,c,(i+p-1) mod H,(j+q-1) mod W],  p, q = 0..2,
+ * with x, W, y stored as BF16 (W laid out [Cout][Cin][3][3]; the input layer's x may be FP32),
+ * bias and every accumulation FP32.
+ * Supported channel pairs (Cin, Cout): (2, 32), (32, 32), (32, 2); H and W multiples of 16;
+ * arrays [B][C][H][W], C-contiguous device memory. */
+#define SGM_CONV_RELU 1      /* apply ReLU to the output */
+#define SGM_CONV_OUT_F32 2   /* y is FP32 (else BF16) */
+#define SGM_CONV_IN_F32 4    /* x is FP32 (else BF16); the 2-channel input layer only */
+/* y = conv(x), options in `flags` (SGM_CONV_*). */
+int sgm_conv3x3_forward(const void* x, const void* w, const float* bias, void* y, int B, int Cin, int Cout,
+                        int H, int W, int flags, void* stream);
+/* gx = d(sum gy * y)/dx for one layer (FP32 gy, gx); when mask (the BF16 layer input, itself a
+ * ReLU output) is non-NULL, gx is zeroed where mask <= 0 (the derivative of that ReLU). */
+int sgm_conv3x3_backward_data(const float* gy, const void* w, const void* mask, float* gx, int B, int Cin,
+                              int Cout, int H, int W, void* stream);
+/* gw += d(sum gy * y)/dW, gb += d(sum gy * y)/dbias (FP32, accumulated with atomics); x as in
+ * the forward call (flags: SGM_CONV_IN_F32). */
+int sgm_conv3x3_backward_weights(const float* gy, const void* x, float* gw, float* gb, int B, int Cin,
+                                 int Cout, int H, int W, int flags, void* stream);
+/* One AdamW step on n FP32 master values w (moments m, v; decoupled weight decay); when w_bf16
+ * is non-NULL the updated values are also written there in BF16.  step >= 1 (bias correction). */
+int sgm_adamw_step(float* w, void* w_bf16, const float* g, float* m, float* v, int64_t n, float lr, float beta1,
+                   float beta2, float eps, float weight_decay, int step, void* stream);
+/* grad = 2 (out - target) / n and *loss += sum (out - target)^2 / n (FP32; *loss accumulated). */
+int sgm_mse_grad(const float* out, const float* target, float* grad, float* loss, int64_t n, void* stream);
+/* Keep the wavenumbers of an Mc x Mc grid from B complex64 Mf x Mf spectral arrays (FFT order). */
+int sgm_spectral_truncate(const void* src, int Mf, void* dst, int Mc, int B, void* stream);
+/* x[b,0] = scale Re u[b], x[b,1] = scale Im u[b] (complex64 -> BF16 channels, B x H x W fields). */
+int sgm_pack_channels(const void* u, void* x, int B, int H, int W, float scale, void* stream);
+/* u[b] += scale (d[b,0] + i d[b,1]) (FP32 channels added to complex64 fields). */
+int sgm_unpack_add(const float* d, void* u, int B, int H, int W, float scale, void* stream);
+
 /*
  * Dirichlet Helmholtz solve that allocates nothing (no counterpart in the paper; it is an
  * interface choice of this library).

@@ -58,3 +58,19 @@ def network_backward(params, acts, gout):
         grads[li] = (gW, gb)
         g = gx
     return grads, g
+
+
+def adamw_step(w, g, m, v, step, lr, beta1, beta2, eps, weight_decay):
+    """One AdamW update (Adam moments, bias correction, decoupled weight decay); returns (w, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mhat = m / (1.0 - beta1 ** step)
+    vhat = v / (1.0 - beta2 ** step)
+    w = w - lr * (mhat / (np.sqrt(vhat) + eps) + weight_decay * w)
+    return w, m, v
+
+
+def mse(out, target):
+    """Mean squared error and its gradient with respect to ``out``."""
+    d = out - target
+    return np.mean(d * d), 2.0 * d / d.size

@@ -90,8 +90,9 @@ cudaError_t launch_cheb(int mode, int basis, bool real, const void* in, void* ou
                         const FftPlan& plan, const cplx<T>* tw, const cplx<T>* dctw, cudaStream_t s,
                         bool wide = false);
 
-// FP64 values per Chebyshev row per thread in the elimination scratch (k_solve.cu).
-int solve_scratch_values(int basis);
+// FP64 values per Chebyshev row per thread in the elimination scratch (k_solve.cu), for nc
+// columns per thread.
+int solve_scratch_values(int basis, int nc);
 // compile-time-length transforms (k_fast_*.cu), for lengths with fast_compiled(L)
 bool fast_compiled(int L);
 template <typename T>
@@ -107,6 +108,6 @@ cudaError_t launch_cheb_fast(int mode, int basis, bool real, const void* in, voi
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out,
                          int N, long ncols, const Wavenumbers& wn, const double* tab, double* scratch,
-                         long scratch_threads, cudaStream_t s);
+                         long scratch_threads, const int2* groups, long ngroups, cudaStream_t s);
 
 }  // namespace sgm

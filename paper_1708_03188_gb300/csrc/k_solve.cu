@@ -29,7 +29,10 @@
 // (-l1, l2) have the same kappa2 and hence the same matrix, so one thread eliminates the
 // pair (NC = 2): the FP64 factorisation (pivots, reciprocals, tail coefficients) is shared
 // and only the right-hand-side recurrences are done per column.  Columns l1 = 0 and
-// l1 = -M1/2 have no partner and are solved as a pair of identical columns.  Warps own 32
+// l1 = -M1/2 have no partner and are solved as a pair of identical columns.  When both
+// Fourier axes have the same length and domain, (l1, l2) and (l2, l1) share kappa2 too and
+// one thread eliminates the four columns (+-a, b), (+-b, a) (NC = 4): fewer FP64 operations
+// per column and about one warp per SM sub-partition on the 256^3 box.  Warps own 32
 // consecutive work items of one parity, so every load and store of a row is coalesced.
 // The per-row reduced quantities go to a global FP64 scratch laid out [row][value][thread]
 // (a warp touches 256 contiguous bytes) and are read back by the back substitution.
@@ -66,26 +69,41 @@ template <typename T> __device__ __forceinline__ void st2(void* p, long i, bool 
   reinterpret_cast<cplx<T>*>(p)[i] = w;
 }
 
-// Column mapping: work item w -> columns (c1, c2).  pair_m1 = 0: c1 = c2 = w (NC = 1).
-// Otherwise (3-D): axis 1 has M1 = pair_m1 entries; group g = w / n2 picks i1 = g for
-// g <= (M1-1)/2 paired with M1 - g, and i1 = M1/2 (even M1) alone.
+// Column mapping: work item -> the NC columns that share one matrix (kappa2).
+//   NC = 1: item = column.
+//   NC = 2 (3-D): axis 1 has M1 = pair_m1 entries; group g = item / n2 picks i1 = g for
+//           g <= (M1-1)/2 paired with M1 - g, and i1 = M1/2 (even M1) alone (then c1 = c2).
+//   NC = 4 (3-D, equal lengths and domains on axes 1 and 2): item -> (a, b) = groups[item],
+//           0 <= a <= b <= M/2, columns (+a, b), (-a, b), (+b, a), (-b, a) in (axis-1 index,
+//           axis-2 index); coinciding columns (a = 0, a = b, a or b = M/2) are solved twice.
 struct ColumnMap {
   long nitems;
   int pair_m1;
   int n2;
+  const int2* groups;
 };
 
-__device__ __forceinline__ void map_columns(const ColumnMap& m, long w, long& c1, long& c2) {
-  if (m.pair_m1 == 0) { c1 = c2 = w; return; }
-  const long g = w / m.n2;
-  const long i2 = w - g * m.n2;
-  const int npairs = (m.pair_m1 - 1) / 2;
-  long i1, j1;
-  if (g == 0) { i1 = j1 = 0; }
-  else if (g <= npairs) { i1 = g; j1 = m.pair_m1 - g; }
-  else { i1 = j1 = m.pair_m1 / 2; }
-  c1 = i1 * m.n2 + i2;
-  c2 = j1 * m.n2 + i2;
+template <int NC> __device__ __forceinline__ void map_columns(const ColumnMap& m, long w, long* c) {
+  if constexpr (NC == 1) {
+    c[0] = w;
+  } else if constexpr (NC == 2) {
+    const long g = w / m.n2;
+    const long i2 = w - g * m.n2;
+    const int npairs = (m.pair_m1 - 1) / 2;
+    long i1, j1;
+    if (g == 0) { i1 = j1 = 0; }
+    else if (g <= npairs) { i1 = g; j1 = m.pair_m1 - g; }
+    else { i1 = j1 = m.pair_m1 / 2; }
+    c[0] = i1 * m.n2 + i2;
+    c[1] = j1 * m.n2 + i2;
+  } else {
+    const int2 ab = m.groups[w];
+    const int M = m.pair_m1;
+    c[0] = (long)ab.x * m.n2 + ab.y;
+    c[1] = (long)((M - ab.x) % M) * m.n2 + ab.y;
+    c[2] = (long)ab.y * m.n2 + ab.x;
+    c[3] = (long)((M - ab.y) % M) * m.n2 + ab.x;
+  }
 }
 
 // table indices (layout written by space.cu)
@@ -118,8 +136,8 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
     const int p = (int)(w & 1);
     const long item = (w >> 1) * 32 + lane;
     if (item >= cm.nitems) continue;
-    long cc[2];
-    map_columns(cm, item, cc[0], cc[1]);
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
     const double k2 = kappa2_of(wn, cc[0]);
     const double aB = b - a * k2;
     const double ell = -aB * half_pi;
@@ -246,8 +264,8 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
     const int p = (int)(w & 1);
     const long item = (w >> 1) * 32 + lane;
     if (item >= cm.nitems) continue;
-    long cc[2];
-    map_columns(cm, item, cc[0], cc[1]);
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
     const double k2 = kappa2_of(wn, cc[0]);
     const double aA = b - 2.0 * a * k2;
     const double aB = fma(a * k2, k2, fma(-b, k2, cc0));
@@ -367,54 +385,61 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
   }
 }
 
-// Values per row per thread in the scratch (NC = 2 upper bound).
-int solve_scratch_values(int basis) { return basis == kDirichlet ? 6 : 9; }
+// Values per row per thread in the scratch for NC columns per thread.
+int solve_scratch_values(int basis, int nc) { return basis == kDirichlet ? 2 + 2 * nc : 5 + 2 * nc; }
 
-template <typename T>
-cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
-                         long ncols, const Wavenumbers& wn, const double* tab, double* scratch,
-                         long scratch_threads, cudaStream_t s) {
-  if (ncols <= 0) return cudaSuccess;
-  ColumnMap cm;
-  cm.pair_m1 = 0;
-  cm.n2 = wn.n2;
-  cm.nitems = ncols;
-  if (wn.n1 > 1) {  // 3-D: pair +l1 / -l1 along axis 1
-    cm.pair_m1 = wn.n1;
-    const long groups = 1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0);
-    cm.nitems = groups * wn.n2;
-  }
+template <typename T, int NC>
+static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
+                            long ncols, const Wavenumbers& wn, const ColumnMap& cm, const double* tab, double* scratch,
+                            long scratch_threads, cudaStream_t s) {
   const long warps_needed = 2 * ((cm.nitems + 31) / 32);
   long threads = std::min(scratch_threads, warps_needed * 32);
-  threads = std::max(128L, (threads / 128) * 128);
+  threads = std::max(128L, ((threads + 127) / 128) * 128);
+  threads = std::min(threads, std::max(128L, (scratch_threads / 128) * 128));
   const unsigned grid = (unsigned)(threads / 128);
   const int ts = N + 8;
   cudaError_t e;
   if (basis == kDirichlet) {
     const size_t smem = sizeof(double) * 2 * ts;
-    if (cm.pair_m1) {
-      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-      k_solve_dirichlet<T, 2><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
-    } else {
-      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-      k_solve_dirichlet<T, 1><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
-    }
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    k_solve_dirichlet<T, NC><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
   } else {
     const size_t smem = sizeof(double) * 13 * ts;
-    if (cm.pair_m1) {
-      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-      k_solve_biharmonic<T, 2><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
-    } else {
-      if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-      k_solve_biharmonic<T, 1><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
-    }
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    k_solve_biharmonic<T, NC><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
   }
   return cudaGetLastError();
 }
 
+// groups: device table of (a, b) for the four-column grouping, or nullptr
+template <typename T>
+cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
+                         long ncols, const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
+                         const int2* groups, long ngroups, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  ColumnMap cm;
+  cm.pair_m1 = 0;
+  cm.n2 = wn.n2;
+  cm.nitems = ncols;
+  cm.groups = groups;
+  if (wn.n1 > 1 && groups) {
+    cm.pair_m1 = wn.n1;
+    cm.nitems = ngroups;
+    return solve_nc<T, 4>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+  }
+  if (wn.n1 > 1) {  // 3-D: pair +l1 / -l1 along axis 1
+    cm.pair_m1 = wn.n1;
+    cm.nitems = (1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0)) * (long)wn.n2;
+    return solve_nc<T, 2>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+  }
+  return solve_nc<T, 1>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+}
+
 template cudaError_t launch_solve<float>(int, bool, double, double, double, const void*, void*, int, long,
-                                         const Wavenumbers&, const double*, double*, long, cudaStream_t);
+                                         const Wavenumbers&, const double*, double*, long, const int2*, long,
+                                         cudaStream_t);
 template cudaError_t launch_solve<double>(int, bool, double, double, double, const void*, void*, int, long,
-                                          const Wavenumbers&, const double*, double*, long, cudaStream_t);
+                                          const Wavenumbers&, const double*, double*, long, const int2*, long,
+                                          cudaStream_t);
 
 }  // namespace sgm

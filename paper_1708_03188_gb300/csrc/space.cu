@@ -391,7 +391,7 @@ int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void
   long ncols = 1;
   for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
   return wrap(launch_solve<T>(basis, s->real_spec, a, b, c, in, out, (int)s->n[0], ncols, wavenumbers(s), s->tab,
-                              s->scratch, s->scratch_threads, st),
+                              s->scratch, s->scratch_threads, s->groups, s->ngroups, st),
               "solve");
 }
 
@@ -437,6 +437,7 @@ void free_space(sgm_space* s) {
   cudaFree(s->W1);
   cudaFree(s->W2);
   cudaFree(s->scratch);
+  cudaFree(s->groups);
   s->magic = 0;
   delete s;
 }
@@ -533,11 +534,32 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       int sms = 0;
       chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
       long ncols = s->nspec / N;
-      long need = 2 * ((ncols + 31) / 32) * 32;
+      long items = ncols;
+      s->solve_nc = 1;
+      if (ndim == 3) {
+        const double L1 = s->dom[3] - s->dom[2], L2 = s->dom[5] - s->dom[4];
+        const bool square = kinds[2] == SGM_FOURIER_R2C && n[1] == n[2] && std::fabs(L1 - L2) <= 1e-12 * std::fabs(L1);
+        if (square) {
+          // columns (+-a, b), (+-b, a) share kappa2: one elimination thread per (a, b), a <= b
+          const int M = (int)n[1], h = M / 2;
+          std::vector<int2> g;
+          for (int a = 0; a <= h; ++a)
+            for (int b = a; b <= h; ++b) g.push_back(make_int2(a, b));
+          s->ngroups = (long)g.size();
+          chk(cudaMalloc(&s->groups, sizeof(int2) * g.size()), "group table");
+          if (st == SGM_OK) chk(cudaMemcpy(s->groups, g.data(), sizeof(int2) * g.size(), cudaMemcpyHostToDevice), "group table");
+          items = s->ngroups;
+          s->solve_nc = 4;
+        } else {
+          items = (1 + (n[1] - 1) / 2 + (n[1] % 2 == 0 ? 1 : 0)) * s->spec[2];
+          s->solve_nc = 2;
+        }
+      }
+      long need = 2 * ((items + 31) / 32) * 32;
       need = ((need + 127) / 128) * 128;
       s->scratch_threads = std::min((long)std::max(1, sms) * 256, need);
       const long rows = N / 2 + 1;
-      const int nv = solve_scratch_values(kinds[0] == SGM_SHEN_DIRICHLET ? kDirichlet : kBiharmonic);
+      const int nv = solve_scratch_values(kinds[0] == SGM_SHEN_DIRICHLET ? kDirichlet : kBiharmonic, s->solve_nc);
       chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
     }
   }

@@ -30,6 +30,9 @@ struct sgm_space {
   void* W2 = nullptr;
   double* scratch = nullptr;
   long scratch_threads = 0;
+  int2* groups = nullptr;    // (a, b) table of the four-column grouping of the eliminations
+  long ngroups = 0;
+  int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
 
   size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
   size_t relem() const { return prec == SGM_F32 ? 4 : 8; }

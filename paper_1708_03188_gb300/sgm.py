@@ -41,6 +41,15 @@ _SIGNATURES = {
     "sgm_batch_destroy": (ctypes.c_int, [_VP]),
     "sgm_batch_offsets": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "sgm_batch_helmholtz": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_conv3x3_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP]),
+    "sgm_conv3x3_backward_data": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 5 + [_VP]),
+    "sgm_conv3x3_backward_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP]),
+    "sgm_adamw_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_int64] + [ctypes.c_float] * 5
+                       + [ctypes.c_int, _VP]),
+    "sgm_mse_grad": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int64, _VP]),
+    "sgm_spectral_truncate": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP]),
+    "sgm_pack_channels": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
+    "sgm_unpack_add": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
     "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int,
                                                    _D, _D, _VP, _VP, _VP]),
@@ -258,3 +267,67 @@ class Batch1D:
             raise ValueError("bad output tensor")
         check(lib().sgm_batch_helmholtz(self._h, _ptr(f), _ptr(out), _stream(stream)))
         return out
+
+
+# ---- learned-closure kernels -------------------------------------------------------------------
+def _vp_or_none(t):
+    return _VP(t.data_ptr()) if t is not None else _VP()
+
+
+CONV_RELU, CONV_OUT_F32, CONV_IN_F32 = 1, 2, 4
+
+
+def conv3x3_forward(x, w, bias, y, relu, stream=None):
+    """y = conv3x3(x) (+ReLU); w BF16, bias FP32, x BF16 (FP32 for a 2-channel input), y BF16 or FP32."""
+    B, Cin, H, W = x.shape
+    Cout = w.shape[0]
+    flags = (CONV_RELU if relu else 0) | (CONV_OUT_F32 if y.dtype == torch.float32 else 0) | \
+        (CONV_IN_F32 if x.dtype == torch.float32 else 0)
+    check(lib().sgm_conv3x3_forward(_ptr(x), _ptr(w), _ptr(bias), _ptr(y), B, Cin, Cout, H, W, flags,
+                                    _stream(stream)))
+    return y
+
+
+def conv3x3_backward_data(gy, w, mask, gx, stream=None):
+    B, Cin, H, W = gx.shape
+    Cout = w.shape[0]
+    check(lib().sgm_conv3x3_backward_data(_ptr(gy), _ptr(w), _vp_or_none(mask), _ptr(gx), B, Cin, Cout, H, W,
+                                          _stream(stream)))
+    return gx
+
+
+def conv3x3_backward_weights(gy, x, gw, gb, stream=None):
+    B, Cin, H, W = x.shape
+    Cout = gw.shape[0]
+    flags = CONV_IN_F32 if x.dtype == torch.float32 else 0
+    check(lib().sgm_conv3x3_backward_weights(_ptr(gy), _ptr(x), _ptr(gw), _ptr(gb), B, Cin, Cout, H, W, flags,
+                                             _stream(stream)))
+
+
+def adamw_step(w, w_bf16, g, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):
+    check(lib().sgm_adamw_step(_ptr(w), _vp_or_none(w_bf16), _ptr(g), _ptr(m), _ptr(v), w.numel(), lr, beta1, beta2,
+                               eps, weight_decay, int(step), _stream(stream)))
+
+
+def mse_grad(out, target, grad, loss, stream=None):
+    check(lib().sgm_mse_grad(_ptr(out), _ptr(target), _ptr(grad), _ptr(loss), out.numel(), _stream(stream)))
+
+
+def spectral_truncate(src, dst, stream=None):
+    """src [B, Mf, Mf] complex64 -> dst [B, Mc, Mc] (wavenumbers of the coarse grid kept)."""
+    B, Mf = src.shape[0], src.shape[-1]
+    Mc = dst.shape[-1]
+    check(lib().sgm_spectral_truncate(_ptr(src), Mf, _ptr(dst), Mc, B, _stream(stream)))
+    return dst
+
+
+def pack_channels(u, x, scale, stream=None):
+    B, H, W = u.shape
+    check(lib().sgm_pack_channels(_ptr(u), _ptr(x), B, H, W, float(scale), _stream(stream)))
+    return x
+
+
+def unpack_add(d, u, scale, stream=None):
+    B, H, W = u.shape
+    check(lib().sgm_unpack_add(_ptr(d), _ptr(u), B, H, W, float(scale), _stream(stream)))
+    return u

@@ -47,3 +47,26 @@ def test_network_gradients_finite_differences():
         xp = x.copy(); xp[idx] += h
         xm = x.copy(); xm[idx] -= h
         assert abs((f(params, xp) - f(params, xm)) / (2 * h) - gx[idx]) < 1e-6
+
+
+def test_adamw_first_step_is_a_signed_step():
+    # with zero moments, the first step moves each weight by lr * (g/|g| approximately + wd w)
+    g = np.array([3.0, -0.5, 1e-3])
+    w = np.array([1.0, 2.0, -1.0])
+    w1, m, v = cnn.adamw_step(w, g, np.zeros(3), np.zeros(3), 1, 0.1, 0.9, 0.999, 1e-12, 0.01)
+    assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+    assert np.allclose(w1, w - 0.1 * (np.sign(g) + 0.01 * w), atol=1e-9)
+
+
+def test_mse_gradient_finite_difference():
+    g = np.random.default_rng(4)
+    out, tgt = g.standard_normal(12), g.standard_normal(12)
+    loss, grad = cnn.mse(out, tgt)
+    assert abs(loss - np.mean((out - tgt) ** 2)) < 1e-15
+    h = 1e-6
+    for i in range(12):
+        o = out.copy(); o[i] += h
+        lp, _ = cnn.mse(o, tgt)
+        o[i] -= 2 * h
+        lm, _ = cnn.mse(o, tgt)
+        assert abs((lp - lm) / (2 * h) - grad[i]) < 1e-8

@@ -96,6 +96,9 @@ SPACES = [
     (["chebyshev", "c2c"], [256, 19]),
     (["dirichlet", "c2c"], [512, 24]),
     (["biharmonic"], [384]),
+    # equal Fourier lengths: the eliminations group the columns (+-a, b), (+-b, a)
+    (["dirichlet", "c2c", "r2c"], [24, 16, 16]),
+    (["biharmonic", "c2c", "r2c"], [20, 9, 9]),
 ]
 
 
@@ -131,7 +134,9 @@ def _column_systems(os_, build):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("kinds,sizes", [(["dirichlet"], [40]), (["dirichlet", "r2c"], [32, 33]),
                                           (["dirichlet", "c2c", "r2c"], [24, 40, 64]),
-                                          (["dirichlet", "c2c"], [65, 9])])
+                                          (["dirichlet", "c2c"], [65, 9]),
+                                          (["dirichlet", "c2c", "r2c"], [24, 16, 16]),
+                                          (["dirichlet", "c2c", "r2c"], [16, 9, 9])])
 @pytest.mark.parametrize("a,b", [(-1.0, 0.0), (1.0, -300.0), (0.5, 2.0), (0.0, 1.0)])
 def test_helmholtz_solve(kinds, sizes, prec, a, b):
     gs = gspace(kinds, sizes, prec)
@@ -153,7 +158,9 @@ def test_helmholtz_solve(kinds, sizes, prec, a, b):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 @pytest.mark.parametrize("kinds,sizes", [(["biharmonic"], [40]), (["biharmonic", "r2c"], [34, 18]),
                                           (["biharmonic", "c2c", "r2c"], [32, 33, 34]),
-                                          (["biharmonic", "c2c"], [67, 9])])
+                                          (["biharmonic", "c2c"], [67, 9]),
+                                          (["biharmonic", "c2c", "r2c"], [32, 16, 16]),
+                                          (["biharmonic", "c2c", "r2c"], [20, 9, 9])])
 @pytest.mark.parametrize("a,b,c", [(1.0, 0.0, 0.0), (1.3, -0.4, 2.0), (0.0, 0.0, 1.0), (0.0, 1.0, -5.0)])
 def test_biharmonic_solve(kinds, sizes, prec, a, b, c):
     gs = gspace(kinds, sizes, prec)
