@@ -152,12 +152,13 @@ def hbm_peak():
 
 
 # FP64 operations (an FMA counts 2) per Chebyshev row per complex Fourier column in the
-# eliminations of k_solve.cu, where the columns +m and -m share one factorisation:
-#   Dirichlet  (15 per row of the shared factorisation) / 2 + 16 per right-hand-side column = 23.5
-#   biharmonic (53 per row of the shared factorisation) / 2 + 34 per right-hand-side column = 60.5
+# eliminations of k_solve.cu on the 256^3 box, where the four columns (+-a, b), (+-b, a) share
+# one factorisation:
+#   Dirichlet  (15 per row of the shared factorisation) / 4 + 16 per right-hand-side column = 19.75
+#   biharmonic (53 per row of the shared factorisation) / 4 + 34 per right-hand-side column = 47.25
 # (row assembly from the coefficient tables, elimination of the sub-diagonal entries, one
 # reciprocal = approximation + cubic Newton step, back substitution with the tail sums).
-FLOPS_PER_ROW = {"dirichlet": 23.5, "biharmonic": 60.5}
+FLOPS_PER_ROW = {"dirichlet": 19.75, "biharmonic": 47.25}
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
 
 
@@ -275,7 +276,7 @@ def run_ours(args):
     fl_p = FLOPS_PER_ROW["dirichlet"] * (N0 - 2) * ncols
     t_b = br["biharmonic_solve_kernel_ms"] * 1e-3
     achieved = fl_b / t_b / 1e12
-    roofline = {"kernel": "k_solve_biharmonic<double,2> (FP64 elimination, 33024 columns x 252 rows)",
+    roofline = {"kernel": "k_solve_biharmonic<double,4> (FP64 elimination, 33024 columns x 252 rows)",
                 "bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
                 "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA probe measured 1.19)",
@@ -309,6 +310,7 @@ def run_ours(args):
 
     gl = gl_measure(Space, stream, steps=args.gl_steps) if args.gl_steps > 0 else None
     batch = batch_measure(stream)
+    closure_res = closure_measure(stream) if args.gl_steps > 0 else None
 
     value = world * DOF_PER_STEP / (ms * 1e-3) / 1e9
     line = None
@@ -335,6 +337,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "gl": gl,
             "batch": batch,
+            "closure": closure_res,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -401,6 +404,59 @@ def batch_measure(stream, reps=20):
                      "launches_per_batch": 3}
         b.close()
     return out
+
+
+def closure_measure(stream, iters=1500):
+    """Learned closure: fine 256^2 runs (integrating-factor RK4, dt 0.01, complex64) truncated to
+    the under-resolved coarse 32^2 grid every 0.05; train on 12 trajectories, judge on a held-out
+    one; time the corrected coarse step against the fine steps covering the same 0.05."""
+    import time as _time
+    import torch
+    from paper_1708_03188_gb300 import closure
+    t0 = _time.time()
+    coarse = closure.CoarseModel(32, 0.05)
+    train_snaps = closure.fine_trajectories(256, 32, 12, 30.0, 30, 0.01, 0.05, first_item=0)
+    test_snaps = closure.fine_trajectories(256, 32, 2, 30.0, 20, 0.01, 0.05, first_item=100)
+    x, tgt = closure.training_pairs(coarse, train_snaps)
+    net = closure.ClosureNet(seed=0)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    hist, scale = closure.train(net, x, tgt, iters=iters, batch=32)
+    b.record(stream)
+    b.synchronize()
+    train_ms = a.elapsed_time(b)
+    e1p, e1l = closure.relative_errors(coarse, net, test_snaps, scale, horizon=1)
+    e4p, e4l = closure.relative_errors(coarse, net, test_snaps, scale, horizon=4)
+    # cost of one corrected coarse step (batch 1) vs the 5 fine steps of the same 0.05
+    u = test_snaps[0, :1].contiguous()
+
+    def timed(fn, reps=20):
+        fn()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    corr_ms = timed(lambda: closure.corrected_step(coarse, net, u, scale))
+    plain_ms = timed(lambda: coarse.step_batch(u))
+    from paper_1708_03188_gb300.sgm import GinzburgLandau, Space
+    spf = Space(["c2c", "c2c"], (256, 256), domain=closure.DOMAIN, precision="f32")
+    glf = GinzburgLandau(spf, 1.5, -0.5, 0.01, "ifrk4")
+    uf = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
+    fine_ms = timed(lambda: glf.step(uf, 5))
+    return {"fine": "256^2, IF-RK4 dt 0.01", "coarse": "32^2, IF-RK4 dt 0.05", "params": net.num_params,
+            "train": {"iters": iters, "batch": 32, "ms_per_iter": round(train_ms / iters, 4),
+                      "loss_first_last": [round(hist[0], 4), round(hist[-1], 4)]},
+            "one_step_rel_error": {"plain": e1p, "learned": e1l},
+            "four_step_rel_error": {"plain": e4p, "learned": e4l},
+            "ms_per_0.05": {"coarse_plain": round(plain_ms, 4), "coarse_learned": round(corr_ms, 4),
+                            "fine_plain": round(fine_ms, 4)},
+            "wall_s": round(_time.time() - t0, 1)}
 
 
 # ---- FP64 CPU oracle on a bounded sample of the same workload ---------------------------------------
