@@ -13,6 +13,31 @@ template <typename T> __host__ __device__ constexpr int fast_elems() { return si
 template <typename T> __host__ __device__ constexpr int fast_tw_cols() { return sizeof(T) == 4 ? 16 : 8; }
 constexpr int kFastThreads = 256;
 
+// Copy TOTAL elements through registers: each thread loads up to 16 of its elements (element
+// idx = threadIdx.x + q * kFastThreads) before storing them, so the loads of a chunk are all in
+// flight at once (a generic global pointer may alias shared memory, so an interleaved
+// load/store loop would wait for every load).  ld(idx) -> value, st(idx, value); both are only
+// called for idx < TOTAL.
+template <int TOTAL, typename C, typename LD, typename ST>
+__device__ __forceinline__ void staged_copy(LD ld, ST st) {
+  constexpr int PER = (TOTAL + kFastThreads - 1) / kFastThreads;
+  constexpr int CH = PER < 16 ? PER : 16;
+#pragma unroll 1
+  for (int q0 = 0; q0 < PER; q0 += CH) {
+    C v[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * kFastThreads;
+      if (q0 + q < PER && idx < TOTAL) v[q] = ld(idx);
+    }
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int idx = threadIdx.x + (q0 + q) * kFastThreads;
+      if (q0 + q < PER && idx < TOTAL) st(idx, v[q]);
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------------------------
 // rows of the contiguous last axis; LF = FFT length (L/2 for packed R2C/C2R, else L)
 template <typename T, int MODE, int LF>
@@ -30,22 +55,34 @@ __global__ void __launch_bounds__(kFastThreads) k_rows_fast(const void* __restri
 
   if (MODE == kRowC2R) {
     const C* src = reinterpret_cast<const C*>(in) + row0 * (H + 1);
-    for (int idx = threadIdx.x; idx < nl * H; idx += kFastThreads) {
-      const int line = idx / H, k = idx - line * H;
-      C x = src[(long)line * (H + 1) + k];
-      C y = src[(long)line * (H + 1) + (H - k)];
-      if (k == 0) { x.y = 0; y.y = 0; }
-      const C yc = cconj(y);
-      const C e = cadd(x, yc);
-      const C o = cmulc(csub(x, yc), __ldg(&tw_L[k]));
-      buf[line * LDP + padi(k)] = mk<C>(e.x - o.y, e.y + o.x);
-    }
+    const int n = nl * H;
+    // stage x_k and x_{H-k} as one pair per element (C2 holds both)
+    struct C2 { C x, y; };
+    staged_copy<LINES * H, C2>(
+        [&](int idx) {
+          C2 r;
+          if (idx < n) {
+            const int line = idx / H, k = idx - line * H;
+            r.x = src[(long)line * (H + 1) + k];
+            r.y = src[(long)line * (H + 1) + (H - k)];
+          }
+          return r;
+        },
+        [&](int idx, C2 v) {
+          if (idx >= n) return;
+          const int line = idx / H, k = idx - line * H;
+          C x = v.x, y = v.y;
+          if (k == 0) { x.y = 0; y.y = 0; }
+          const C yc = cconj(y);
+          const C e = cadd(x, yc);
+          const C o = cmulc(csub(x, yc), __ldg(&tw_L[k]));
+          buf[line * LDP + padi(k)] = mk<C>(e.x - o.y, e.y + o.x);
+        });
   } else {
     const C* src = reinterpret_cast<const C*>(in) + row0 * LF;   // packed real rows are LF complex
-    for (int idx = threadIdx.x; idx < nl * LF; idx += kFastThreads) {
-      const int line = idx / LF, e = idx - line * LF;
-      buf[line * LDP + padi(e)] = src[idx];
-    }
+    const int n = nl * LF;
+    staged_copy<LINES * LF, C>([&](int idx) { return idx < n ? src[idx] : mk<C>((T)0, (T)0); },
+                               [&](int idx, C v) { if (idx < n) buf[(idx / LF) * LDP + padi(idx % LF)] = v; });
   }
   __syncthreads();
   constexpr bool INV = (MODE == kRowC2R || MODE == kRowC2CInv);
@@ -87,10 +124,15 @@ __global__ void __launch_bounds__(kFastThreads) k_strided_fast(const cplx<T>* in
   const int nt = (int)min((long)TW, inner - t0);
   const C* src = in + o * L * inner + t0;
   C* dst = out + o * L * inner + t0;
-  for (int idx = threadIdx.x; idx < L * TW; idx += kFastThreads) {
-    const int i = idx / TW, t = idx % TW;
-    if (t < nt) buf[t * LDP + padi(i)] = src[(long)i * inner + t];
-  }
+  staged_copy<L * TW, C>(
+      [&](int idx) {
+        const int i = idx / TW, t = idx % TW;
+        return t < nt ? src[(long)i * inner + t] : mk<C>((T)0, (T)0);
+      },
+      [&](int idx, C v) {
+        const int i = idx / TW, t = idx % TW;
+        if (t < nt) buf[t * LDP + padi(i)] = v;
+      });
   __syncthreads();
   fft_fast<L, TW, kFastThreads, INV>(buf, nt, twf);
   const T s = INV ? (T)1 : (T)1 / (T)L;
@@ -122,14 +164,17 @@ __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restri
   auto reord = [](int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); };
 
   if (MODE == kChebScalar || MODE == kChebForwardT) {
-    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
-      const int j = idx / TW, t = idx % TW;
-      if (t < nt) {
-        const long g = (long)j * inner + t0 + t;
-        const C v = real ? mk<C>(reinterpret_cast<const T*>(in)[g], (T)0) : reinterpret_cast<const C*>(in)[g];
-        buf[t * LDP + padi(reord(j))] = v;
-      }
-    }
+    staged_copy<N * TW, C>(
+        [&](int idx) {
+          const int j = idx / TW, t = idx % TW;
+          if (t >= nt) return mk<C>((T)0, (T)0);
+          const long g = (long)j * inner + t0 + t;
+          return real ? mk<C>(reinterpret_cast<const T*>(in)[g], (T)0) : reinterpret_cast<const C*>(in)[g];
+        },
+        [&](int idx, C v) {
+          const int j = idx / TW, t = idx % TW;
+          if (t < nt) buf[t * LDP + padi(reord(j))] = v;
+        });
     __syncthreads();
     fft_fast<N, TW, kFastThreads, false>(buf, nt, twf);
     // moments, computed in registers and written back in place
@@ -181,14 +226,16 @@ __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restri
       }
     }
   } else {  // backward
-    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
-      const int k = idx / TW, t = idx % TW;
-      if (t < nt) {
-        const C v = (k < nb) ? from_spec<TS, C>(reinterpret_cast<const TS*>(in), (long)k * inner + t0 + t, real)
-                             : mk<C>((T)0, (T)0);
-        buf[t * LDP + padi(k)] = v;
-      }
-    }
+    staged_copy<N * TW, C>(
+        [&](int idx) {
+          const int k = idx / TW, t = idx % TW;
+          return (t < nt && k < nb) ? from_spec<TS, C>(reinterpret_cast<const TS*>(in), (long)k * inner + t0 + t, real)
+                                    : mk<C>((T)0, (T)0);
+        },
+        [&](int idx, C v) {
+          const int k = idx / TW, t = idx % TW;
+          if (t < nt) buf[t * LDP + padi(k)] = v;
+        });
     __syncthreads();
     C a[PER];
 #pragma unroll

@@ -57,11 +57,13 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_pad(const cplx<T>* __r
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int r0 = blockIdx.x * LINES;
   const int nl = min(LINES, M - r0);
-  for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
-    const int line = idx / MP, q = idx - line * MP;
-    const int j = gl_origidx<M, MP>(q);
-    buf[line * LDP + padi(q)] = j >= 0 ? U[(long)(r0 + line) * M + j] : mk<C>((T)0, (T)0);
-  }
+  staged_copy<LINES * MP, C>(
+      [&](int idx) {
+        const int line = idx / MP, q = idx - line * MP;
+        const int j = gl_origidx<M, MP>(q);
+        return (idx < nl * MP && j >= 0) ? U[(long)(r0 + line) * M + j] : mk<C>((T)0, (T)0);
+      },
+      [&](int idx, C v) { if (idx < nl * MP) buf[(idx / MP) * LDP + padi(idx % MP)] = v; });
   __syncthreads();
   fft_fast<MP, LINES, kFastThreads, true>(buf, nl, twf);
   for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
@@ -80,13 +82,16 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_cols(cplx<T>* __restrict__ 
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int c0 = blockIdx.x * TW;
   const int nt = min(TW, MP - c0);
-  for (int idx = threadIdx.x; idx < MP * TW; idx += kFastThreads) {
-    const int q = idx / TW, t = idx % TW;
-    if (t < nt) {
-      const int j = gl_origidx<M, MP>(q);
-      buf[t * LDP + padi(q)] = j >= 0 ? P[(long)j * MP + c0 + t] : mk<C>((T)0, (T)0);
-    }
-  }
+  staged_copy<MP * TW, C>(
+      [&](int idx) {
+        const int q = idx / TW, t = idx % TW;
+        const int j = gl_origidx<M, MP>(q);
+        return (t < nt && j >= 0) ? P[(long)j * MP + c0 + t] : mk<C>((T)0, (T)0);
+      },
+      [&](int idx, C v) {
+        const int q = idx / TW, t = idx % TW;
+        if (t < nt) buf[t * LDP + padi(q)] = v;
+      });
   __syncthreads();
   fft_fast<MP, TW, kFastThreads, true>(buf, nt, twf);
   const T g = (T)gamma;
@@ -120,10 +125,9 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int r0 = blockIdx.x * LINES;
   const int nl = min(LINES, M - r0);
-  for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
-    const int line = idx / MP, q = idx - line * MP;
-    buf[line * LDP + padi(q)] = P[(long)(r0 + line) * MP + q];
-  }
+  staged_copy<LINES * MP, C>(
+      [&](int idx) { return idx < nl * MP ? P[(long)r0 * MP + idx] : mk<C>((T)0, (T)0); },
+      [&](int idx, C v) { if (idx < nl * MP) buf[(idx / MP) * LDP + padi(idx % MP)] = v; });
   __syncthreads();
   fft_fast<MP, LINES, kFastThreads, false>(buf, nl, twf);
   const T inv = (T)1 / (T)MP;
