@@ -73,6 +73,9 @@ extern "C" {
 /* precision */
 #define SGM_F32 1                /* FP32 transforms, FP64 eliminations */
 #define SGM_F64 2                /* FP64 everywhere */
+/* Chebyshev-axis method, or-ed into the precision of an SGM_F32 space (see sgm_space_create) */
+#define SGM_CHEB_TC 0x10         /* dense BF16x3 tensor-core contraction (N <= 128) */
+#define SGM_CHEB_AUTO 0x20       /* time both methods at creation and keep the faster */
 
 /* shape selectors for sgm_space_shape */
 #define SGM_PHYSICAL 0
@@ -96,7 +99,20 @@ const char* sgm_status_string(int status);
  *              and [0, 2 pi) on a Fourier axis.  A Fourier axis of length L = hi - lo is
  *              mapped onto [0, 2 pi), so its derivatives scale by 2 pi / L (Sec. 6).
  *              A Chebyshev axis must keep [-1, 1].
- *   precision  SGM_F32 or SGM_F64.
+ *   precision  SGM_F32 or SGM_F64.  An SGM_F32 space with a Chebyshev axis of N <= 128
+ *              points may add one Chebyshev-axis method flag:
+ *                SGM_CHEB_TC    the Chebyshev-axis scalar product, forward T_k transform and
+ *                               backward transform run as one dense N x N contraction per
+ *                               column on the tensor cores (tcgen05, BF16x3 split products,
+ *                               FP32 accumulation) instead of the DCT-via-FFT kernels.
+ *                               Error: each product carries at most ~3 * 2^-16 relative
+ *                               error (the dropped lo*lo product and the BF16 rounding of
+ *                               the lo parts), ~2^-18 relative L2 per contraction in
+ *                               practice; SGM_ERR_SIZE if N > 128.
+ *                SGM_CHEB_AUTO  time both methods on this space at creation (on a private
+ *                               stream, device-synchronising) and keep the faster; N > 128
+ *                               keeps the FFT method.
+ *              The flags are an SGM_ERR_ARG for SGM_F64 spaces.
  * Allocates device tables and workspace on the current device (freed by destroy).
  */
 int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n,
@@ -105,6 +121,15 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
 int sgm_space_destroy(sgm_space* space);
 /* Write the ndim extents of the PHYSICAL or SPECTRAL array into shape_out. */
 int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out);
+/* Chebyshev-axis method in use: *method = 0 (DCT via FFT), 1 (tensor-core contraction). */
+int sgm_space_cheb_method(const sgm_space* space, int* method);
+/*
+ * Number of bounded waits inside tensor-core kernels on the current device that gave up
+ * (each wait gives up after ~1 s; the kernel then skips its result and returns).  Reads a
+ * device counter synchronously; reset != 0 also zeroes it.  A non-zero count means the
+ * results of those launches are invalid.
+ */
+int sgm_tc_wait_timeouts(int* count, int reset);
 
 /*
  * Scalar product S(F(f)) (the `inner(v, f)` of Sec. 3.4.2 and the right-hand side

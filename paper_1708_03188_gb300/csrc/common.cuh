@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace sgm {
 
 // ---- complex arithmetic on float2 / double2 -------------------------------------------
@@ -104,6 +106,17 @@ cudaError_t launch_strided_fast(bool inverse, const void* in, void* out, long ou
 template <typename T>
 cudaError_t launch_cheb_fast(int mode, int basis, bool real, const void* in, void* out, int N, long inner,
                              const cplx<T>* twf, const cplx<T>* dctw, cudaStream_t s, bool wide);
+
+// dense Chebyshev-axis contraction on the tensor cores (k_cheb_tc.cu), N <= 128: input and
+// output are [N][ncols] real arrays (complex data as interleaved real columns); img is the
+// device copy of tc_cheb_image(mode, basis, N)
+template <typename TI, typename TO>
+cudaError_t launch_cheb_tc(const void* in, void* out, long ncols, int N, const void* img, cudaStream_t s);
+constexpr int kTcMaxN = 128;
+int tc_pad16(int n);
+// number of uint16 in the image is 2 * tc_pad16(N)^2
+std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N);
+int tc_timeouts(bool reset);
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out,

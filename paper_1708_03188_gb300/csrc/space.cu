@@ -340,9 +340,26 @@ template <typename T> int fourier_backward(sgm_space* s, const void* in, void* o
               "rows backward");
 }
 
+// the Chebyshev-axis pass as the dense tensor-core contraction (FP32 spaces)
+int cheb_pass_tc(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide) {
+  const int N = (int)s->n[0];
+  long ncols = s->real_spec ? 1 : 2;
+  for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
+  const void* img = s->tc_img[mode];
+  cudaError_t e;
+  if (mode == kChebBackward)
+    e = wide ? launch_cheb_tc<double, float>(in, out, ncols, N, img, st)
+             : launch_cheb_tc<float, float>(in, out, ncols, N, img, st);
+  else
+    e = wide ? launch_cheb_tc<float, double>(in, out, ncols, N, img, st)
+             : launch_cheb_tc<float, float>(in, out, ncols, N, img, st);
+  return wrap(e, "chebyshev contraction");
+}
+
 template <typename T>
 int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide = false) {
   const int N = (int)s->n[0];
+  if (sizeof(T) == 4 && s->cheb_tc) return cheb_pass_tc(s, mode, in, out, st, wide);
   long inner = 1;
   for (int i = 1; i < s->ndim; ++i) inner *= s->spec[i];
   FftPlan p = make_plan(N);
@@ -438,8 +455,52 @@ void free_space(sgm_space* s) {
   cudaFree(s->W2);
   cudaFree(s->scratch);
   cudaFree(s->groups);
+  for (void* p : s->tc_img) cudaFree(p);
   s->magic = 0;
   delete s;
+}
+
+// time the scalar product and backward passes of both Chebyshev-axis methods on this space's
+// workspaces (the pair that the physical-to-physical solves run), keep the faster method;
+// returns 1 (contraction), 0 (FFT) or -1 (CUDA error, message set)
+int autotune_cheb(sgm_space* s) {
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int result = -1;
+  float best[2] = {0, 0};
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    fail(SGM_ERR_CUDA, "autotune: stream or event creation failed");
+    goto done;
+  }
+  if (cudaMemsetAsync(s->W1, 0, (size_t)s->nspec * s->celem(), st) != cudaSuccess ||
+      cudaMemsetAsync(s->W2, 0, (size_t)s->nspec * 16, st) != cudaSuccess) {
+    fail(SGM_ERR_CUDA, "autotune: workspace clear failed");
+    goto done;
+  }
+  for (int m = 0; m < 2; ++m) {
+    s->cheb_tc = m;
+    best[m] = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+      if (cudaEventRecord(e0, st) != cudaSuccess) goto cuda_fail;
+      if (cheb_pass<float>(s, kChebScalar, s->W1, s->W2, st, true) != SGM_OK) goto done;
+      if (cheb_pass<float>(s, kChebBackward, s->W2, s->W1, st, true) != SGM_OK) goto done;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) goto cuda_fail;
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) goto cuda_fail;
+      if (rep > 0 && ms < best[m]) best[m] = ms;   // the first run includes one-time set-up
+    }
+  }
+  result = best[1] < best[0] ? 1 : 0;
+  goto done;
+cuda_fail:
+  fail(SGM_ERR_CUDA, "autotune: %s", cudaGetErrorString(cudaGetLastError()));
+done:
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (result < 0) s->cheb_tc = 0;
+  return result;
 }
 
 }  // namespace
@@ -468,7 +529,11 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (!out || !kinds || !n) return fail(SGM_ERR_NULL, "out, kinds and n must be non-NULL");
   *out = nullptr;
   if (ndim < 1 || ndim > 3) return fail(SGM_ERR_SIZE, "ndim must be 1..3 (got %d)", ndim);
+  const int cheb_flags = precision & (SGM_CHEB_TC | SGM_CHEB_AUTO);
+  precision &= ~(SGM_CHEB_TC | SGM_CHEB_AUTO);
   if (precision != SGM_F32 && precision != SGM_F64) return fail(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
+  if (cheb_flags == (SGM_CHEB_TC | SGM_CHEB_AUTO)) return fail(SGM_ERR_ARG, "SGM_CHEB_TC and SGM_CHEB_AUTO exclude each other");
+  if (cheb_flags && precision != SGM_F32) return fail(SGM_ERR_ARG, "Chebyshev-axis method flags need an SGM_F32 space");
   const bool cheb = kinds[0] == SGM_CHEBYSHEV || kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC;
   for (int d = 0; d < ndim; ++d) {
     const int k = kinds[d];
@@ -481,6 +546,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "biharmonic basis needs N >= 6");
   if (kinds[0] == SGM_CHEBYSHEV && n[0] < 2) return fail(SGM_ERR_SIZE, "Chebyshev basis needs N >= 2");
   if (kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] < 2) return fail(SGM_ERR_SIZE, "R2C axis needs M >= 2");
+  if ((cheb_flags & SGM_CHEB_TC) && (!cheb || n[0] > kTcMaxN))
+    return fail(SGM_ERR_SIZE, "SGM_CHEB_TC needs a Chebyshev axis of at most %d points", kTcMaxN);
   if (cheb && domain && (domain[0] != -1.0 || domain[1] != 1.0))
     return fail(SGM_ERR_ARG, "the Chebyshev axis domain must be [-1, 1]");
   if (domain)
@@ -563,11 +630,37 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
     }
   }
+  if (st == SGM_OK && cheb && cheb_flags && n[0] <= kTcMaxN) {
+    const int N = (int)n[0];
+    for (int mode : {kChebScalar, kChebBackward, kChebForwardT}) {
+      const std::vector<uint16_t> img = tc_cheb_image(mode, kinds[0], N);
+      chk(cudaMalloc(&s->tc_img[mode], img.size() * 2), "contraction matrix");
+      if (st == SGM_OK)
+        chk(cudaMemcpy(s->tc_img[mode], img.data(), img.size() * 2, cudaMemcpyHostToDevice), "contraction matrix");
+    }
+    if (st == SGM_OK) s->cheb_tc = (cheb_flags & SGM_CHEB_TC) ? 1 : autotune_cheb(s);
+    if (s->cheb_tc < 0) st = SGM_ERR_CUDA;
+  }
   if (st != SGM_OK) {
     free_space(s);
     return st;
   }
   *out = s;
+  return SGM_OK;
+}
+
+int sgm_space_cheb_method(const sgm_space* space, int* method) {
+  if (!space || !method) return fail(SGM_ERR_NULL, "NULL argument");
+  if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  *method = space->cheb_tc;
+  return SGM_OK;
+}
+
+int sgm_tc_wait_timeouts(int* count, int reset) {
+  if (!count) return fail(SGM_ERR_NULL, "NULL argument");
+  const int v = tc_timeouts(reset != 0);
+  if (v < 0) return fail(SGM_ERR_CUDA, "reading the device wait counter failed");
+  *count = v;
   return SGM_OK;
 }
 

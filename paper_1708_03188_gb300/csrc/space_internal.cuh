@@ -33,6 +33,8 @@ struct sgm_space {
   int2* groups = nullptr;    // (a, b) table of the four-column grouping of the eliminations
   long ngroups = 0;
   int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
+  int cheb_tc = 0;           // 1: Chebyshev axis by the tensor-core contraction (k_cheb_tc.cu)
+  void* tc_img[3] = {nullptr, nullptr, nullptr};  // contraction matrices per ChebMode
 
   size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
   size_t relem() const { return prec == SGM_F32 ? 4 : 8; }

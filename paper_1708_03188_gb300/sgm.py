@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libsgm.so")
 
 KINDS = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2, "c2c": 3, "r2c": 4}
 PRECISION = {"f32": 1, "f64": 2}
+CHEB_METHOD = {"fft": 0, "tc": 0x10, "auto": 0x20}
 _VP = ctypes.c_void_p
 _D = ctypes.c_double
 
@@ -25,6 +26,8 @@ _SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int]),
     "sgm_space_destroy": (ctypes.c_int, [_VP]),
     "sgm_space_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
+    "sgm_space_cheb_method": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "sgm_tc_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "sgm_scalar_product": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sgm_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sgm_backward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -97,10 +100,12 @@ class Space:
     """Tensor-product space (one Chebyshev axis 0 + Fourier axes, or Fourier axes only).
 
     kinds: names from KINDS; sizes: quadrature points per axis; domain: [(lo, hi)] per
-    axis or None; precision "f32" (FP32 transforms, FP64 solves) or "f64".
+    axis or None; precision "f32" (FP32 transforms, FP64 solves) or "f64"; cheb (f32 only):
+    "fft" (DCT via FFT), "tc" (dense BF16x3 tensor-core contraction, N <= 128) or "auto"
+    (the faster of the two, timed at creation).
     """
 
-    def __init__(self, kinds, sizes, domain=None, precision="f32"):
+    def __init__(self, kinds, sizes, domain=None, precision="f32", cheb="fft"):
         self.kinds = tuple(kinds)
         self.sizes = tuple(int(s) for s in sizes)
         self.precision = precision
@@ -112,7 +117,8 @@ class Space:
             flat = [float(v) for pair in domain for v in pair]
             dom = (_D * len(flat))(*flat)
         self._h = _VP()
-        check(lib().sgm_space_create(ctypes.byref(self._h), nd, k, n, dom, PRECISION[precision]))
+        check(lib().sgm_space_create(ctypes.byref(self._h), nd, k, n, dom,
+                                     PRECISION[precision] | CHEB_METHOD[cheb]))
         self.physical_shape = self._shape(0)
         self.spectral_shape = self._shape(1)
         cheb = self.kinds[0] in ("chebyshev", "dirichlet", "biharmonic")
@@ -127,6 +133,13 @@ class Space:
         out = (ctypes.c_int64 * len(self.kinds))()
         check(lib().sgm_space_shape(self._h, which, out))
         return tuple(int(v) for v in out)
+
+    @property
+    def cheb_method(self):
+        """"tc" if the Chebyshev axis runs as the tensor-core contraction, else "fft"."""
+        m = ctypes.c_int()
+        check(lib().sgm_space_cheb_method(self._h, ctypes.byref(m)))
+        return "tc" if m.value else "fft"
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -331,3 +344,10 @@ def unpack_add(d, u, scale, stream=None):
     B, H, W = u.shape
     check(lib().sgm_unpack_add(_ptr(d), _ptr(u), B, H, W, float(scale), _stream(stream)))
     return u
+
+
+def tc_wait_timeouts(reset=False):
+    """Bounded waits in tensor-core kernels that gave up on this device (0 when healthy)."""
+    c = ctypes.c_int()
+    check(lib().sgm_tc_wait_timeouts(ctypes.byref(c), 1 if reset else 0))
+    return c.value
