@@ -19,14 +19,19 @@
 //     registers and stored transposed to the K-major layout, one 16-byte core-matrix row per
 //     store (conflict-free: a warp writes 512 contiguous bytes);
 //   * one thread issues 3 * Kp / 16 MMAs into a 128 x Np FP32 TMEM accumulator and commits to
-//     an mbarrier; the 4 warps then read back their 32 TMEM lanes (= 32 consecutive columns)
+//     an mbarrier; the warps then read back their TMEM lanes (32 consecutive columns per warp)
 //     with tcgen05.ld and store each output row as one coalesced 128-byte (FP32) or 256-byte
-//     (FP64) access.
+//     (FP64) access;
+//   * the CTAs are persistent (one to four per SM), load the matrix once, and double-buffer
+//     the tiles and the TMEM accumulators so that the MMAs of one tile overlap the epilogue of
+//     the previous one and the loads of the next.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "common.cuh"
+#include "convert.cuh"
 #include "tc.cuh"
 
 namespace sgm {
@@ -37,27 +42,41 @@ namespace {
 
 constexpr int kTcCols = 128;  // data columns per CTA = MMA M = TMEM lanes
 
-template <typename T> __device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
+__device__ __forceinline__ float as_f32(float x) { return x; }
+__device__ __forceinline__ float as_f32(double x) { return narrow_f64(x); }
+
+// FP32 accumulator to the output type (exact widening on the integer pipe for FP64)
+template <typename TO> __device__ __forceinline__ TO from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ double from_f32<double>(float v) { return widen_f32(v); }
+
+__device__ __forceinline__ uint32_t pack2(uint16_t a, uint16_t b) {
   return (uint32_t)a | ((uint32_t)b << 16);
 }
 
+constexpr int kTcThreads = 512;  // 4 threads per column in the load phase, 16 warps
+
+// Persistent: each CTA loads the matrix once, then walks over column tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Tile i (local count) is staged into A[i % 2] and multiplied into
+// TMEM accumulator i % 2; its epilogue runs in the next iteration, while the tensor cores work on
+// tile i + 1 and the loads of tile i + 2 are in flight behind the epilogue's stores.
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(128) k_cheb_tc(const TI* __restrict__ in, TO* __restrict__ out, long ncols,
-                                                 int nin, int nout, int Kp, int Np, int tcols,
-                                                 const unsigned char* __restrict__ img) {
+__global__ void __launch_bounds__(kTcThreads) k_cheb_tc(const TI* __restrict__ in, TO* __restrict__ out,
+                                                        long ncols, int nin, int nout, int Kp, int Np, int tcols,
+                                                        const unsigned char* __restrict__ img) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[3];   // [0] matrix copy, [1] / [2] MMA of even / odd tiles
   __shared__ uint32_t tmem_slot;
   const int tid = threadIdx.x, warp = tid >> 5;
-  unsigned char* Ah = smem;                     // 128 columns x Kp, BF16 hi
-  unsigned char* Al = Ah + 256 * Kp;            // lo
-  unsigned char* Bh = Al + 256 * Kp;            // Np x Kp hi, then lo (the image)
+  const uint32_t abytes = 256u * (uint32_t)Kp;              // one BF16 part of a 128-column tile
+  unsigned char* Bm = smem;                                 // matrix: Np x Kp hi, then lo
   const uint32_t half_img = (uint32_t)Np * (uint32_t)Kp * 2;
+  unsigned char* A0 = smem + 2 * half_img;                  // tile buffers: [buf][hi | lo]
   const uint32_t lboA = (kTcCols / 8) * 128, lboB = (uint32_t)Np * 16;
+  const long ntiles = (ncols + kTcCols - 1) / kTcCols;
 
   if (tid == 0) {
-    tc::mbar_init(&bar[0], 1);
-    tc::mbar_init(&bar[1], 1);
+    for (int i = 0; i < 3; ++i) tc::mbar_init(&bar[i], 1);
     tc::fence_mbar_init();
   }
   if (warp == 0) tc::tmem_alloc(&tmem_slot, (uint32_t)tcols);
@@ -67,74 +86,107 @@ __global__ void __launch_bounds__(128) k_cheb_tc(const TI* __restrict__ in, TO* 
   const uint32_t tmem = tmem_slot;
   if (tid == 0) {
     tc::mbar_arrive_expect_tx(&bar[0], 2 * half_img);
-    tc::bulk_g2s(Bh, img, 2 * half_img, &bar[0]);
+    tc::bulk_g2s(Bm, img, 2 * half_img, &bar[0]);
   }
+  bool ok = true;   // thread 0: every wait so far succeeded
 
-  // stage column c = c0 + tid: rows j -> K-major core-matrix rows of 8 BF16
-  const long c = (long)blockIdx.x * kTcCols + tid;
-  const bool cv = c < ncols;
-  const uint32_t row_off = (uint32_t)(tid >> 3) * 128 + (uint32_t)(tid & 7) * 16;
-#pragma unroll 2
-  for (int kg = 0; kg < Kp / 8; ++kg) {
-    TI x[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int j = kg * 8 + i;
-      x[i] = (cv && j < nin) ? in[(long)j * ncols + c] : (TI)0;
-    }
-    uint16_t h[8], l[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) tc::split_bf16(x[i], h[i], l[i]);
-    const uint32_t off = row_off + (uint32_t)kg * lboA;
-    *reinterpret_cast<uint4*>(Ah + off) = make_uint4(pack2<TI>(h[0], h[1]), pack2<TI>(h[2], h[3]),
-                                                     pack2<TI>(h[4], h[5]), pack2<TI>(h[6], h[7]));
-    *reinterpret_cast<uint4*>(Al + off) = make_uint4(pack2<TI>(l[0], l[1]), pack2<TI>(l[2], l[3]),
-                                                     pack2<TI>(l[4], l[5]), pack2<TI>(l[6], l[7]));
-  }
-  tc::fence_proxy_async();
-  __syncthreads();
+  // load phase: column m, K groups kq, kq + 4, ...
+  const int m = tid & (kTcCols - 1), kq = tid >> 7;
+  const uint32_t row_off = (uint32_t)(m >> 3) * 128 + (uint32_t)(m & 7) * 16;
+  // epilogue: TMEM lane quarter warp % 4 (32 columns), output-row chunks q = warp / 4 (mod 4)
+  const int lq = warp & 3, qs = warp >> 2;
+  const int ngroups = Kp / 8, nchunks = Np / 16;
 
-  bool loaded = true;
-  if (tid == 0) {
-    loaded = tc::mbar_wait(&bar[0], 0);
-    if (!loaded) {
-      atomicAdd(&g_tc_timeouts, 1);
-    } else {
-      const uint32_t idesc = tc::idesc_bf16(kTcCols, Np);
-      const uint32_t ah = tc::smem_addr(Ah), al = tc::smem_addr(Al);
-      const uint32_t bh = tc::smem_addr(Bh), bl = bh + half_img;
-      for (int s = 0; s < Kp / 16; ++s) {
-        const uint32_t oa = (uint32_t)s * 2 * lboA, ob = (uint32_t)s * 2 * lboB;
-        const uint64_t dah = tc::smem_desc(ah + oa, lboA, 128), dal = tc::smem_desc(al + oa, lboA, 128);
-        const uint64_t dbh = tc::smem_desc(bh + ob, lboB, 128), dbl = tc::smem_desc(bl + ob, lboB, 128);
-        tc::mma_bf16(tmem, dal, dbh, idesc, s > 0 ? 1u : 0u);
-        tc::mma_bf16(tmem, dah, dbl, idesc, 1u);
-        tc::mma_bf16(tmem, dah, dbh, idesc, 1u);
-      }
-    }
-    tc::mma_commit(&bar[1]);
-  }
-  bool done = tc::mbar_wait(&bar[1], 0);
-  done = __all_sync(0xffffffffu, done) != 0;
-  if (!done && (tid & 31) == 0) atomicAdd(&g_tc_timeouts, 1);
-  tc::fence_after_sync();
-  if (done) {
-    const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int q = 0; q < Np / 16; ++q) {
+  auto epilogue = [&](long tile, int buf) {
+    const long c = tile * kTcCols + lq * 32 + (tid & 31);
+    const uint32_t base = tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(buf * (tcols / 2));
+    for (int q = qs; q < nchunks; q += 4) {
       float v[16];
-      tc::tmem_ld16(lane_base + (uint32_t)(q * 16), v);
-      if (cv) {
+      tc::tmem_ld16(base + (uint32_t)(q * 16), v);
+      if (c < ncols) {
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
           const int k = q * 16 + i;
-          if (k < nout) out[(long)k * ncols + c] = (TO)v[i];
+          if (k < nout) out[(long)k * ncols + c] = from_f32<TO>(v[i]);
         }
       }
     }
+  };
+
+  long prev = -1;
+  int i = 0;
+  for (long t = blockIdx.x; t < ntiles; t += gridDim.x, ++i) {
+    const int buf = i & 1;
+    unsigned char* Ah = A0 + (uint32_t)buf * 2 * abytes;
+    unsigned char* Al = Ah + abytes;
+    const long c = t * kTcCols + m;
+    const bool cv = c < ncols;
+#pragma unroll 2
+    for (int kg = kq; kg < ngroups; kg += 4) {
+      TI x[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        const int j = kg * 8 + r;
+        x[r] = (cv && j < nin) ? in[(long)j * ncols + c] : (TI)0;
+      }
+      uint16_t h[8], l[8];
+      // FP64 input is first rounded to FP32 on the integer pipe (its residual, 2^-24, is far
+      // below the 2^-16 of the split); FP64 conversions would run at 1/64 of the FP32 rate
+#pragma unroll
+      for (int r = 0; r < 8; ++r) tc::split_bf16(as_f32(x[r]), h[r], l[r]);
+      const uint32_t off = row_off + (uint32_t)kg * lboA;
+      *reinterpret_cast<uint4*>(Ah + off) =
+          make_uint4(pack2(h[0], h[1]), pack2(h[2], h[3]), pack2(h[4], h[5]), pack2(h[6], h[7]));
+      *reinterpret_cast<uint4*>(Al + off) =
+          make_uint4(pack2(l[0], l[1]), pack2(l[2], l[3]), pack2(l[4], l[5]), pack2(l[6], l[7]));
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) {
+      tc::fence_after_sync();
+      if (i == 0) ok = tc::mbar_wait(&bar[0], 0);
+      if (ok) {
+        const uint32_t idesc = tc::idesc_bf16(kTcCols, Np);
+        const uint32_t ah = tc::smem_addr(Ah), al = tc::smem_addr(Al);
+        const uint32_t bh = tc::smem_addr(Bm), bl = bh + half_img;
+        const uint32_t d = tmem + (uint32_t)(buf * (tcols / 2));   // accumulators tcols / 2 >= Np apart
+        for (int s = 0; s < Kp / 16; ++s) {
+          const uint32_t oa = (uint32_t)s * 2 * lboA, ob = (uint32_t)s * 2 * lboB;
+          const uint64_t dah = tc::smem_desc(ah + oa, lboA, 128), dal = tc::smem_desc(al + oa, lboA, 128);
+          const uint64_t dbh = tc::smem_desc(bh + ob, lboB, 128), dbl = tc::smem_desc(bl + ob, lboB, 128);
+          tc::mma_bf16(d, dal, dbh, idesc, s > 0 ? 1u : 0u);
+          tc::mma_bf16(d, dah, dbl, idesc, 1u);
+          tc::mma_bf16(d, dah, dbh, idesc, 1u);
+        }
+      }
+      tc::mma_commit(&bar[1 + buf]);   // arrives at once if nothing was issued
+    }
+    if (prev >= 0) {
+      const int pb = (i - 1) & 1;
+      bool done = tc::mbar_wait(&bar[1 + pb], (uint32_t)(((i - 1) >> 1) & 1));
+      done = __all_sync(0xffffffffu, done) != 0;
+      if (!done && (tid & 31) == 0) atomicAdd(&g_tc_timeouts, 1);
+      tc::fence_after_sync();
+      if (done) epilogue(prev, pb);
+      tc::fence_before_sync();
+    }
+    prev = t;
+  }
+  if (prev >= 0) {
+    const int pb = (i - 1) & 1;
+    bool done = tc::mbar_wait(&bar[1 + pb], (uint32_t)(((i - 1) >> 1) & 1));
+    done = __all_sync(0xffffffffu, done) != 0;
+    if (!done && (tid & 31) == 0) atomicAdd(&g_tc_timeouts, 1);
+    tc::fence_after_sync();
+    if (done) epilogue(prev, pb);
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (tid == 0 && !loaded) tc::mbar_wait(&bar[0], 0);   // let a late bulk copy land before exit
+  if (tid == 0 && !ok) {
+    atomicAdd(&g_tc_timeouts, 1);
+    tc::mbar_wait(&bar[0], 0);   // let a late bulk copy land before exit
+  }
   if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)tcols);
 }
 
@@ -200,21 +252,29 @@ std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N) {
   return img;
 }
 
-// shared memory of one CTA: the X tile and the matrix, BF16 hi and lo parts
-size_t tc_cheb_smem(int Kp, int Np) { return (size_t)512 * Kp + (size_t)4 * Np * Kp; }
+// shared memory of one CTA: the matrix and two X tiles, BF16 hi and lo parts each
+size_t tc_cheb_smem(int Kp, int Np) { return (size_t)4 * Np * Kp + (size_t)2 * 512 * Kp; }
 
 template <typename TI, typename TO>
 cudaError_t launch_cheb_tc(const void* in, void* out, long ncols, int N, const void* img, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   const int Kp = tc_pad16(N), Np = tc_pad16(N);
   int tcols = 32;
-  while (tcols < Np) tcols *= 2;
+  while (tcols < 2 * Np) tcols *= 2;   // two accumulators of Np FP32 columns
   const size_t smem = tc_cheb_smem(Kp, Np);
   cudaError_t e = cudaFuncSetAttribute(k_cheb_tc<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const unsigned grid = (unsigned)((ncols + kTcCols - 1) / kTcCols);
-  k_cheb_tc<TI, TO><<<grid, 128, smem, s>>>((const TI*)in, (TO*)out, ncols, N, N, Kp, Np, tcols,
-                                            (const unsigned char*)img);
+  int dev = 0, sms = 0, per_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cheb_tc<TI, TO>, kTcThreads, smem)) != cudaSuccess)
+    return e;
+  // TMEM: at most 512 columns per SM among the resident CTAs
+  per_sm = std::max(1, std::min(per_sm, 512 / tcols));
+  const long ntiles = (ncols + kTcCols - 1) / kTcCols;
+  const unsigned grid = (unsigned)std::min(ntiles, (long)sms * per_sm);
+  k_cheb_tc<TI, TO><<<grid, kTcThreads, smem, s>>>((const TI*)in, (TO*)out, ncols, N, N, Kp, Np, tcols,
+                                                   (const unsigned char*)img);
   return cudaGetLastError();
 }
 
