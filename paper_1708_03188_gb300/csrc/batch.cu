@@ -21,12 +21,16 @@ struct BatchProblemH {  // host mirror of BatchProblem in k_batch.cu
   int tw_off;
   int dct_off;
   int plan;
+  int L;
+  int chirp_off;
+  int bhat_off;
 };
 size_t batch_problem_bytes();
 template <typename T>
-cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int Nmax, const void* probs,
+cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int ldb, const void* probs,
                          const int* by_slot, const void* plans, const void* pool, const long* wbase, double* S,
-                         double* U, double* scratch, const long* sbase, cudaStream_t s);
+                         double* U, double* scratch, const long* sbase, const void* coef, const double* mass,
+                         cudaStream_t s);
 
 }  // namespace sgm
 
@@ -38,6 +42,8 @@ struct sgm_batch {
   int device = 0;
   int prec = SGM_F64;
   int nprob = 0, Nmax = 0;
+  int ldb = 0;                    // shared-memory buffer length of the transform kernels
+  int nbluestein = 0;             // problems whose DFT runs as a Bluestein convolution
   long total = 0;                 // sum of N
   std::vector<int64_t> offsets;   // nprob + 1
   void* probs = nullptr;
@@ -49,6 +55,8 @@ struct sgm_batch {
   double* S = nullptr;
   double* U = nullptr;
   double* scratch = nullptr;
+  double* coef = nullptr;         // (-2 pi (k+1)(k+2), -4 pi (k+1)) per row k < Nmax
+  double* mass = nullptr;         // B_kk: 3 pi / 2 for k = 0, else pi
 };
 
 namespace {
@@ -63,6 +71,8 @@ void free_batch(sgm_batch* b) {
   cudaFree(b->S);
   cudaFree(b->U);
   cudaFree(b->scratch);
+  cudaFree(b->coef);
+  cudaFree(b->mass);
   b->magic = 0;
   delete b;
 }
@@ -78,6 +88,74 @@ template <typename T> void push_twiddles(std::vector<cplx<T>>& pool, int N, long
   }
 }
 
+int largest_prime_factor(int n) {
+  int best = 1;
+  for (int p = 2; p * p <= n; ++p)
+    while (n % p == 0) {
+      best = p;
+      n /= p;
+    }
+  return n > 1 ? std::max(best, n) : best;
+}
+
+// sizes with a prime factor above this run their DFT as a Bluestein convolution
+constexpr int kBluesteinPrime = 32;
+
+// in-place radix-2 DFT of a power-of-two length (exp(-2 pi i j k / L)), long double
+void host_fft(std::vector<long double>& re, std::vector<long double>& im) {
+  const size_t L = re.size();
+  for (size_t i = 1, j = 0; i < L; ++i) {
+    size_t bit = L >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      std::swap(re[i], re[j]);
+      std::swap(im[i], im[j]);
+    }
+  }
+  const long double pi = 3.141592653589793238462643383279502884L;
+  for (size_t len = 2; len <= L; len <<= 1) {
+    for (size_t i = 0; i < L; i += len)
+      for (size_t k = 0; k < len / 2; ++k) {
+        const long double a = -2.0L * pi * (long double)k / (long double)len;
+        const long double wr = cosl(a), wi = sinl(a);
+        const size_t u = i + k, v = i + k + len / 2;
+        const long double xr = re[v] * wr - im[v] * wi, xi = re[v] * wi + im[v] * wr;
+        re[v] = re[u] - xr;
+        im[v] = im[u] - xi;
+        re[u] += xr;
+        im[u] += xi;
+      }
+  }
+}
+
+// Bluestein tables of length N with convolution length L: chirp c_n = exp(-i pi n^2 / N)
+// (n^2 reduced modulo 2N exactly), then FFT_L of b (b_n = conj c_n, b_{L-n} = b_n) divided by L
+template <typename T> void push_bluestein(std::vector<cplx<T>>& pool, int N, int L, int& chirp_off, int& bhat_off) {
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> cr(N), ci(N);
+  for (long n = 0; n < N; ++n) {
+    const long m = (n * n) % (2L * N);
+    const long double a = -pi * (long double)m / (long double)N;
+    cr[n] = cosl(a);
+    ci[n] = sinl(a);
+  }
+  chirp_off = (int)pool.size();
+  for (int n = 0; n < N; ++n) pool.push_back(mk<cplx<T>>((T)cr[n], (T)ci[n]));
+  std::vector<long double> br(L, 0.0L), bi(L, 0.0L);
+  for (int n = 0; n < N; ++n) {
+    br[n] = cr[n];
+    bi[n] = -ci[n];
+    if (n > 0) {
+      br[L - n] = cr[n];
+      bi[L - n] = -ci[n];
+    }
+  }
+  host_fft(br, bi);
+  bhat_off = (int)pool.size();
+  for (int m = 0; m < L; ++m) pool.push_back(mk<cplx<T>>((T)(br[m] / L), (T)(bi[m] / L)));
+}
+
 template <typename T> int build(sgm_batch* b, const int64_t* n, const double* alpha) {
   const int P = b->nprob;
   std::vector<int> order(P);
@@ -86,20 +164,33 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   std::map<int, int> size_index;   // N -> plan index
   std::vector<FftPlan> plans;
   std::vector<cplx<T>> pool;
-  std::vector<int> tw_off, dct_off;
+  std::vector<int> tw_off, dct_off, conv_len, chirp_off, bhat_off;
   std::vector<BatchProblemH> probs(P);
+  b->ldb = b->Nmax + 1;
   for (int p = 0; p < P; ++p) {
     const int N = (int)n[p];
     if (!size_index.count(N)) {
       size_index[N] = (int)plans.size();
-      plans.push_back(host_plan(N));
+      int L = 0, co = 0, bo = 0;
+      if (largest_prime_factor(N) > kBluesteinPrime) {
+        L = 1;
+        while (L < 2 * N - 1) L *= 2;
+        b->ldb = std::max(b->ldb, L);
+      }
+      const int Lf = L ? L : N;
+      plans.push_back(host_plan(Lf));
       tw_off.push_back((int)pool.size());
-      push_twiddles<T>(pool, N, (long double)N / 2.0L);    // exp(-2 pi i k / N)
+      push_twiddles<T>(pool, Lf, (long double)Lf / 2.0L);  // exp(-2 pi i k / Lf)
       dct_off.push_back((int)pool.size());
       push_twiddles<T>(pool, N, 2.0L * N);                 // exp(-i pi k / (2N))
+      if (L) push_bluestein<T>(pool, N, L, co, bo);
+      conv_len.push_back(L);
+      chirp_off.push_back(co);
+      bhat_off.push_back(bo);
     }
     const int pi = size_index[N];
-    probs[p] = {N, 0, (long)b->offsets[p], alpha[p], tw_off[pi], dct_off[pi], pi};
+    probs[p] = {N, 0, (long)b->offsets[p], alpha[p], tw_off[pi], dct_off[pi], pi, conv_len[pi], chirp_off[pi], bhat_off[pi]};
+    if (conv_len[pi]) ++b->nbluestein;
   }
   std::vector<int> by_slot(P);
   for (int s = 0; s < P; ++s) {
@@ -114,7 +205,7 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
     wbase[w + 1] = wbase[w] + (long)Nw * 32;
     sbase[w + 1] = sbase[w] + (long)(Nw / 2 + 1) * 96;
   }
-  static_assert(sizeof(BatchProblemH) == 40, "BatchProblem layout");
+  static_assert(sizeof(BatchProblemH) == 48, "BatchProblem layout");
   if (batch_problem_bytes() != sizeof(BatchProblemH)) return set_error(SGM_ERR_STATE, "problem table layout");
   cudaError_t e = cudaSuccess;
   auto up = [&](void** dst, const void* src, size_t bytes) {
@@ -128,6 +219,17 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   up(&b->pool, pool.data(), sizeof(cplx<T>) * pool.size());
   up((void**)&b->wbase, wbase.data(), sizeof(long) * wbase.size());
   up((void**)&b->sbase, sbase.data(), sizeof(long) * sbase.size());
+  {
+    const long double pi = 3.141592653589793238462643383279502884L;
+    std::vector<double> coef(2 * (size_t)b->Nmax), mass(b->Nmax);
+    for (int k = 0; k < b->Nmax; ++k) {
+      coef[2 * k] = (double)(-2.0L * pi * (k + 1) * (k + 2));
+      coef[2 * k + 1] = (double)(-4.0L * pi * (k + 1));
+      mass[k] = (double)(k == 0 ? 1.5L * pi : pi);
+    }
+    up((void**)&b->coef, coef.data(), sizeof(double) * coef.size());
+    up((void**)&b->mass, mass.data(), sizeof(double) * mass.size());
+  }
   if (e == cudaSuccess) e = cudaMalloc(&b->S, sizeof(double) * wbase[nw]);
   if (e == cudaSuccess) e = cudaMalloc(&b->U, sizeof(double) * wbase[nw]);
   if (e == cudaSuccess) e = cudaMalloc(&b->scratch, sizeof(double) * 2 * sbase[nw]);
@@ -199,10 +301,10 @@ int sgm_batch_helmholtz(sgm_batch* b, const void* f, void* u, void* stream) {
   if (pa < pb + bytes && pb < pa + bytes) return set_error(SGM_ERR_ALIAS, "f and u overlap");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = b->prec == SGM_F32
-                      ? launch_batch<float>(f, u, b->nprob, b->nprob, b->Nmax, b->probs, b->by_slot, b->plans, b->pool,
-                                            b->wbase, b->S, b->U, b->scratch, b->sbase, s)
-                      : launch_batch<double>(f, u, b->nprob, b->nprob, b->Nmax, b->probs, b->by_slot, b->plans, b->pool,
-                                             b->wbase, b->S, b->U, b->scratch, b->sbase, s);
+                      ? launch_batch<float>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
+                                            b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s)
+                      : launch_batch<double>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
+                                             b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s);
   if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
   return SGM_OK;
 }

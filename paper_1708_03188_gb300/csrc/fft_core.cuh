@@ -148,4 +148,40 @@ __device__ C* fft_lines(C* A, C* B, int nlines, int ld, const FftPlan& p, const 
   return A;
 }
 
+// Bluestein (chirp-z) DFT of one line of length N via a circular convolution of length L, a
+// length with a fast plan (L >= 2N - 1).  With the chirp c_n = exp(-i pi n^2 / N), the identity
+// j k = (j^2 + k^2 - (k - j)^2) / 2 turns the forward DFT into
+//     X_k = c_k sum_j (x_j c_j) conj(c_{k-j}),
+// a convolution of a_j = x_j c_j with b_n = conj(c_|n|); the inverse DFT conjugates every chirp.
+// chirp[n] (n < N) holds c_n; bhat[m] (m < L) holds FFT_L(b) / L with b circularly wrapped
+// (b_{L-n} = b_n); for the inverse, FFT_L(conj b)_m = conj(bhat[(L - m) mod L]).
+// The line's N values are in A; A and B hold >= L elements.  Returns the buffer holding the N
+// results.  Ends with __syncthreads().
+template <bool INV, typename C>
+__device__ C* bluestein(C* A, C* B, int N, int L, const FftPlan& pL, const C* __restrict__ twL,
+                        const C* __restrict__ chirp, const C* __restrict__ bhat) {
+  for (int j = threadIdx.x; j < L; j += blockDim.x) {
+    C v = mk<C>(0, 0);
+    if (j < N) v = cmul(A[j], twiddle(chirp, j, INV));
+    A[j] = v;
+  }
+  __syncthreads();
+  C* Y = fft_lines<false>(A, B, 1, L, pL, twL);
+  for (int m = threadIdx.x; m < L; m += blockDim.x) {
+    C h;
+    if (INV) {
+      h = __ldg(&bhat[m == 0 ? 0 : L - m]);
+      h.y = -h.y;
+    } else {
+      h = __ldg(&bhat[m]);
+    }
+    Y[m] = cmul(Y[m], h);
+  }
+  __syncthreads();
+  C* R = fft_lines<true>(Y, Y == A ? B : A, 1, L, pL, twL);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) R[k] = cmul(R[k], twiddle(chirp, k, INV));
+  __syncthreads();
+  return R;
+}
+
 }  // namespace sgm

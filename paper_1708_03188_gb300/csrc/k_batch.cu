@@ -6,7 +6,9 @@
 // Work decomposition for GB300, where an FP64 warp-instruction occupies its sub-partition's
 // FP64 pipe for ~64 cycles whatever the number of active lanes:
 //   K_A  one CTA per problem: DCT-II of the real samples via one complex FFT (runtime-radix
-//        engine, any N), Dirichlet stencil S_k = t_k - t_{k+2}; S_k is written in FP64 into a
+//        engine; a size with a prime factor above 32 runs its DFT as Bluestein's chirp-z
+//        convolution of a power-of-two length instead of an O(N p) generic-radix pass),
+//        Dirichlet stencil S_k = t_k - t_{k+2}; S_k is written in FP64 into a
 //        warp-interleaved layout [warp][row][lane] (problems sorted by N, 32 per warp).
 //   K_B  one thread per (problem, parity): the FP64 elimination of k_solve.cu's Dirichlet
 //        kernel with kappa = 0, lanes = 32 problems of similar size, so every FP64 instruction
@@ -24,9 +26,12 @@ struct BatchProblem {
   int slot;       // position in the size-sorted order: warp = slot / 32, lane = slot % 32
   long offset;    // first element of f_p / u_p in the caller's arrays
   double alpha;
-  int tw_off;     // exp(-2 pi i k / N), k < N, in the twiddle pool
+  int tw_off;     // exp(-2 pi i k / N), k < N (or / L, k < L with Bluestein), in the twiddle pool
   int dct_off;    // exp(-i pi k / (2N)), k < N, in the twiddle pool
-  int plan;       // index into the plan table
+  int plan;       // index into the plan table (of length N, or of L with Bluestein)
+  int L;          // 0: direct FFT of length N; else Bluestein convolution length
+  int chirp_off;  // Bluestein: exp(-i pi n^2 / N), n < N, in the twiddle pool
+  int bhat_off;   // Bluestein: FFT_L of the wrapped conjugate chirp, / L, in the twiddle pool
 };
 
 // interleaved FP64 arrays: element (row k, slot s) at wbase[s / 32] + k * 32 + s % 32
@@ -38,18 +43,19 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_batch_dct(const T* __restrict__ f, const BatchProblem* __restrict__ probs,
                                                    const int* __restrict__ by_slot, const FftPlan* __restrict__ plans,
                                                    const cplx<T>* __restrict__ pool, const long* __restrict__ wbase,
-                                                   double* __restrict__ S, int Nmax) {
+                                                   double* __restrict__ S, int ldb) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BatchProblem pr = probs[by_slot[blockIdx.x]];   // largest problems first
   const int N = pr.N;
   C* A = reinterpret_cast<C*>(smem_raw);
-  C* B = A + (Nmax + 1);
+  C* B = A + ldb;
   for (int j = threadIdx.x; j < N; j += blockDim.x)
     A[(j & 1) ? N - 1 - (j >> 1) : (j >> 1)] = mk<C>(f[pr.offset + j], (T)0);
   __syncthreads();
   const FftPlan plan = plans[pr.plan];
-  C* V = fft_lines<false>(A, B, 1, Nmax + 1, plan, pool + pr.tw_off);
+  C* V = pr.L ? bluestein<false>(A, B, N, pr.L, plan, pool + pr.tw_off, pool + pr.chirp_off, pool + pr.bhat_off)
+              : fft_lines<false>(A, B, 1, ldb, plan, pool + pr.tw_off);
   C* M = (V == A) ? B : A;
   const C* dctw = pool + pr.dct_off;
   const T scale = (T)3.14159265358979323846 / (T)N;
@@ -71,11 +77,15 @@ __device__ __forceinline__ double rcp64b(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
-// thread = (slot, parity); U (interleaved) receives the Shen coefficients
+// thread = (slot, parity); U (interleaved) receives the Shen coefficients.
+// coef[k] = (-2 pi (k+1)(k+2), -4 pi (k+1)) (the diagonal and the constant upper entries of the
+// Dirichlet stiffness rows) and mass[k] = B_kk (3 pi / 2 for k = 0, else pi) come from host
+// tables: the row coefficients cost loads instead of six FP64 instructions on the critical path.
 __global__ void __launch_bounds__(128) k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ by_slot,
                                                      const long* __restrict__ wbase, const double* __restrict__ S,
                                                      double* __restrict__ U, double* __restrict__ scratch,
-                                                     const long* __restrict__ sbase, int nslots) {
+                                                     const long* __restrict__ sbase, int nslots,
+                                                     const double2* __restrict__ coef, const double* __restrict__ mass) {
   const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // global warp
   const int lane = threadIdx.x & 31;
   const int wslot = w >> 1;          // slot warp
@@ -92,13 +102,20 @@ __global__ void __launch_bounds__(128) k_batch_solve(const BatchProblem* __restr
   double* s = scratch + sbase[wslot] * 2 + (long)p * (sbase[wslot + 1] - sbase[wslot]) + lane;
   double pr_ = 0.0, pg = 0.0, pge = 0.0, pf = 0.0;
   double fn = n > 0 ? S[rbase + (long)p * 32] : 0.0;
+  double2 cn = n > 0 ? __ldg(&coef[p]) : make_double2(0.0, 0.0);
+  double mn = n > 0 ? __ldg(&mass[p]) : 0.0;
   for (int i = 0; i < n; ++i) {
     const int k = p + 2 * i;
     double f = fn;
-    if (i + 1 < n) fn = S[rbase + (long)(k + 2) * 32];
-    const double kp1 = (double)(k + 1);
-    double d = -2.0 * pi * kp1 * (kp1 + 1.0) + aB * (k == 0 ? 1.5 * pi : pi);
-    double g = -4.0 * pi * kp1;
+    const double2 c = cn;
+    const double mk2 = mn;
+    if (i + 1 < n) {
+      fn = S[rbase + (long)(k + 2) * 32];
+      cn = __ldg(&coef[k + 2]);
+      mn = __ldg(&mass[k + 2]);
+    }
+    double d = fma(aB, mk2, c.x);
+    double g = c.y;
     if (i > 0) {
       const double mu = ell * pr_;
       d = fma(-mu, pge, d);
@@ -113,10 +130,21 @@ __global__ void __launch_bounds__(128) k_batch_solve(const BatchProblem* __restr
     pr_ = r; pg = g; pge = g + ell; pf = f;
   }
   double un = 0.0, Ts = 0.0;
+  double rn = 0.0, gn = 0.0, fb = 0.0;
+  if (n > 0) {
+    rn = s[-96];
+    gn = s[-64];
+    fb = s[-32];
+  }
   for (int i = n - 1; i >= 0; --i) {
     const int k = p + 2 * i;
     s -= 96;
-    const double r = s[0], g = s[32], f = s[64];
+    const double r = rn, g = gn, f = fb;
+    if (i > 0) {   // prefetch the row above
+      rn = s[-96];
+      gn = s[-64];
+      fb = s[-32];
+    }
     Ts += un;
     const double u = fma(-g, Ts, fma(-ell, un, f)) * r;
     U[rbase + (long)k * 32] = u;
@@ -128,13 +156,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_batch_idct(T* __restrict__ u, const BatchProblem* __restrict__ probs,
                                                     const int* __restrict__ by_slot, const FftPlan* __restrict__ plans,
                                                     const cplx<T>* __restrict__ pool, const long* __restrict__ wbase,
-                                                    const double* __restrict__ U, int Nmax) {
+                                                    const double* __restrict__ U, int ldb) {
   using C = cplx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const BatchProblem pr = probs[by_slot[blockIdx.x]];   // largest problems first
   const int N = pr.N, nb = N - 2;
   C* A = reinterpret_cast<C*>(smem_raw);
-  C* B = A + (Nmax + 1);
+  C* B = A + ldb;
   for (int k = threadIdx.x; k < N; k += blockDim.x)
     B[k] = mk<C>(k < nb ? narrow<T>(U[ilv(wbase, pr.slot, k)]) : (T)0, (T)0);
   __syncthreads();
@@ -153,16 +181,18 @@ __global__ void __launch_bounds__(256) k_batch_idct(T* __restrict__ u, const Bat
   }
   __syncthreads();
   const FftPlan plan = plans[pr.plan];
-  C* R = fft_lines<true>(B, A, 1, Nmax + 1, plan, pool + pr.tw_off);
+  C* R = pr.L ? bluestein<true>(B, A, N, pr.L, plan, pool + pr.tw_off, pool + pr.chirp_off, pool + pr.bhat_off)
+              : fft_lines<true>(B, A, 1, ldb, plan, pool + pr.tw_off);
   for (int j = threadIdx.x; j < N; j += blockDim.x) u[pr.offset + j] = R[(j & 1) ? N - 1 - (j >> 1) : (j >> 1)].x;
 }
 
 template <typename T>
-cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int Nmax, const void* probs,
+cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int ldb, const void* probs,
                          const int* by_slot, const void* plans, const void* pool, const long* wbase, double* S,
-                         double* U, double* scratch, const long* sbase, cudaStream_t s) {
+                         double* U, double* scratch, const long* sbase, const void* coef, const double* mass,
+                         cudaStream_t s) {
   if (nprob <= 0) return cudaSuccess;
-  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)(Nmax + 1);
+  const size_t smem = 2 * sizeof(cplx<T>) * (size_t)ldb;
   cudaError_t e;
   if (smem > 48 * 1024) {
     if ((e = cudaFuncSetAttribute(k_batch_dct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
@@ -170,18 +200,21 @@ cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int Nmax
   }
   const BatchProblem* P = (const BatchProblem*)probs;
   k_batch_dct<T><<<nprob, 256, smem, s>>>((const T*)f, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, S,
-                                          Nmax);
+                                          ldb);
   const int warps = 2 * ((nslots + 31) / 32);
-  k_batch_solve<<<(warps + 3) / 4, 128, 0, s>>>(P, by_slot, wbase, S, U, scratch, sbase, nslots);
+  k_batch_solve<<<(warps + 3) / 4, 128, 0, s>>>(P, by_slot, wbase, S, U, scratch, sbase, nslots,
+                                                (const double2*)coef, mass);
   k_batch_idct<T><<<nprob, 256, smem, s>>>((T*)u, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, U,
-                                           Nmax);
+                                           ldb);
   return cudaGetLastError();
 }
 
 template cudaError_t launch_batch<float>(const void*, void*, int, int, int, const void*, const int*, const void*,
-                                         const void*, const long*, double*, double*, double*, const long*, cudaStream_t);
+                                         const void*, const long*, double*, double*, double*, const long*, const void*,
+                                         const double*, cudaStream_t);
 template cudaError_t launch_batch<double>(const void*, void*, int, int, int, const void*, const int*, const void*,
-                                          const void*, const long*, double*, double*, double*, const long*, cudaStream_t);
+                                          const void*, const long*, double*, double*, double*, const long*, const void*,
+                                          const double*, cudaStream_t);
 
 size_t batch_problem_bytes() { return sizeof(BatchProblem); }
 

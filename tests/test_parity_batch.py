@@ -43,7 +43,8 @@ def run(sizes, alpha, fs, prec):
 @pytest.mark.parametrize("prec", ["f64", "f32"])
 def test_mixed_sizes(prec):
     g = np.random.default_rng(7)
-    sizes = [16, 17, 4, 5, 31, 64, 97, 128, 200, 256, 211, 13, 40, 6] * 3 + [512, 1021, 768, 2048]
+    # 37, 74, 97, 211, 1021 have a prime factor above 32 (Bluestein DFT)
+    sizes = [16, 17, 4, 5, 31, 64, 97, 128, 200, 256, 211, 13, 40, 6, 37, 74] * 3 + [512, 1021, 768, 2048]
     alpha = g.uniform(0, 1e4, len(sizes))
     alpha[:3] = 0.0                              # pure Poisson problems too
     fs = [np.polynomial.chebyshev.chebval(inputs.cheb_points(N), g.standard_normal(N) * np.exp(-8.0 * np.arange(N) / N))
