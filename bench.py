@@ -378,30 +378,64 @@ def gl_measure(Space, stream, M=512, steps=200):
 
 
 def batch_measure(stream, reps=20):
-    """4096 independent 1-D Dirichlet Helmholtz problems u'' - alpha u = f (sizes log-uniform in
-    [16, 2048], alpha ~ U(0, 1e4), seeded), one sgm_batch_helmholtz call (3 launches) per batch."""
+    """The batched workload: 4096 independent 1-D Dirichlet Helmholtz problems u'' - alpha u = f
+    (sizes log-uniform in [16, 2048], alpha ~ U(0, 1e4)) plus 64 2-D Poisson problems -lap u = f
+    on Shen-Dirichlet x R2C grids (square, sides from {64, ..., 1024}), seeded, solved as ONE
+    captured CUDA graph launch per batch (sgm_batch_run).  Also timed: the 1-D problems alone
+    (three launches, sgm_batch_helmholtz), and the same batch issued call by call on one stream
+    (sgm_helmholtz per 2-D problem, no graph)."""
     import torch
     from paper_1708_03188_gb300 import inputs
-    from paper_1708_03188_gb300.sgm import Batch1D
-    sizes, alpha, fs = inputs.batch1d(4096)
-    out = {"problems": 4096, "dof": int(sizes.sum()), "N_range": [int(sizes.min()), int(sizes.max())]}
-    for prec in ("f32", "f64"):
-        b = Batch1D(sizes, alpha, prec)
-        f = torch.from_numpy(np.concatenate(fs)).to(b.dtype).cuda()
-        u = torch.empty_like(f)
+    from paper_1708_03188_gb300.sgm import Batch, Space
+
+    def timed(fn):
         for _ in range(3):
-            b.solve(f, out=u)
+            fn()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         e = torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for _ in range(reps):
-            b.solve(f, out=u)
+            fn()
         e.record(stream)
         e.synchronize()
-        ms = a.elapsed_time(e) / reps
-        out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round(int(sizes.sum()) / (ms * 1e-3) / 1e9, 4),
-                     "launches_per_batch": 3}
+        return a.elapsed_time(e) / reps
+
+    sizes, alpha, fs = inputs.batch1d(4096)
+    sizes2d, fs2 = inputs.batch2d(64)
+    dof1 = int(sizes.sum())
+    dof2 = int(sum(N * M for N, M in sizes2d))
+    out = {"problems_1d": 4096, "dof_1d": dof1, "N_range_1d": [int(sizes.min()), int(sizes.max())],
+           "problems_2d": 64, "dof_2d": dof2, "sides_2d": sorted({N for N, _ in sizes2d})}
+    for prec in ("f32", "f64"):
+        b = Batch(sizes, alpha, prec)
+        b.add_2d(sizes2d, -1.0, 0.0)
+        f1 = torch.from_numpy(np.concatenate(fs)).to(b.dtype).cuda()
+        u1 = torch.empty_like(f1)
+        buf = np.zeros(b.offsets2d[-1])
+        for q, f in enumerate(fs2):
+            buf[b.offsets2d[q]:b.offsets2d[q] + f.size] = f.ravel()
+        f2 = torch.from_numpy(buf).to(b.dtype).cuda()
+        u2 = torch.empty_like(f2)
+        ms = timed(lambda: b.run(f1, f2, out1=u1, out2=u2, stream=stream))
+        ms1 = timed(lambda: b.solve(f1, out=u1, stream=stream))
+        spaces = [Space(["dirichlet", "r2c"], (N, M), precision=prec) for N, M in sizes2d]
+        views = [(f2[b.offsets2d[q]:b.offsets2d[q] + N * M].view(N, M), u2[b.offsets2d[q]:b.offsets2d[q] + N * M].view(N, M))
+                 for q, (N, M) in enumerate(sizes2d)]
+
+        def serial():
+            b.solve(f1, out=u1, stream=stream)
+            for sp, (fv, uv) in zip(spaces, views):
+                sp.helmholtz(-1.0, 0.0, fv, out=uv, stream=stream)
+        ms_serial = timed(serial)
+        out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round((dof1 + dof2) / (ms * 1e-3) / 1e9, 3),
+                     "graph_launches_per_batch": 1,
+                     "one_d_only": {"ms": round(ms1, 4), "gdof_s": round(dof1 / (ms1 * 1e-3) / 1e9, 3),
+                                    "launches": 3},
+                     "call_by_call_no_graph": {"ms": round(ms_serial, 4),
+                                               "gdof_s": round((dof1 + dof2) / (ms_serial * 1e-3) / 1e9, 3)}}
+        for sp in spaces:
+            sp.close()
         b.close()
     return out
 

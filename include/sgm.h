@@ -222,7 +222,8 @@ typedef struct sgm_batch sgm_batch;
  * discretised with the Shen-Dirichlet basis (Sec. 3.4.2; the weak form of sgm_helmholtz_solve
  * with a = 1, b = -alpha_p, kappa = 0).  precision SGM_F32 (FP32 transforms, FP64
  * eliminations) or SGM_F64.  Builds the size-sorted problem table, per-size FFT plans and
- * twiddles and the FP64 work buffers on the current device.
+ * twiddles and the FP64 work buffers on the current device.  nprob may be 0 (n and alpha
+ * are then ignored) for a batch of 2-D problems only (sgm_batch_add_2d).
  */
 int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double* alpha, int precision);
 int sgm_batch_destroy(sgm_batch* batch);
@@ -235,6 +236,34 @@ int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets);
  * warp), stencil + DCT-III per problem.  f and u must not overlap.
  */
 int sgm_batch_helmholtz(sgm_batch* batch, const void* f, void* u, void* stream);
+/*
+ * Add nprob independent 2-D problems  a lap(u_q) + b u_q = f_q  on [-1, 1] x [0, 2 pi), each
+ * on its own Shen-Dirichlet x R2C Fourier space (the 2-D Poisson problem of Sec. 4, solved as
+ * sgm_helmholtz does: scalar product, per-wavenumber FP64 elimination, backward transform).
+ * sizes: 2 per problem (N >= 4 Chebyshev points, M >= 2 Fourier points, both <= 4096).  One
+ * space per problem is created on the current device, with SGM_CHEB_AUTO for SGM_F32 batches
+ * (the Chebyshev-axis method of each size is chosen by timing).  a, b as in sgm_helmholtz,
+ * common to the problems added by this call.  May be called once per batch, before the first
+ * sgm_batch_run.
+ */
+int sgm_batch_add_2d(sgm_batch* batch, int nprob, const int64_t* sizes, double a, double b);
+/*
+ * Element offsets of the 2-D problems in their packed real arrays (nprob + 1 entries): problem
+ * q's row-major N x M samples start at offsets[q], a multiple of 4, so every problem is 16-byte
+ * aligned; offsets[nprob] is the total length.
+ */
+int sgm_batch_offsets_2d(const sgm_batch* batch, int64_t* offsets);
+/*
+ * Solve every problem of the batch (1-D: f1 -> u1 as sgm_batch_helmholtz; 2-D: f2 -> u2) as ONE
+ * CUDA graph launch on `stream`.  The first call, and any call whose four pointers differ from
+ * those of the captured graph, runs each problem once eagerly (so that every lazily built
+ * table exists), then captures the graph on internal streams: the 1-D kernels on one branch and
+ * the 2-D problems spread over up to 8 concurrent branches, longest first; that call
+ * synchronises the device.  Later calls only launch the graph (asynchronous).  f1/u1 may be NULL
+ * when the batch has no 1-D problems, f2/u2 when it has no 2-D problems.  Calls on one batch
+ * must not overlap.
+ */
+int sgm_batch_run(sgm_batch* batch, const void* f1, void* u1, const void* f2, void* u2, void* stream);
 
 /* ---- learned closure kernels (no counterpart in the paper) -----------------------------------
  * A periodic 3x3 convolution layer is the circular cross-correlation

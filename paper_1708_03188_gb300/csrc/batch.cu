@@ -1,6 +1,7 @@
-// batch.cu - host side of the batched 1-D Helmholtz problems (kernels in k_batch.cu):
-// problem table sorted by size, per-size FFT plans and twiddle pools, warp-interleaved FP64
-// buffers, and the C ABI entry points sgm_batch_*.
+// batch.cu - host side of the batched problems (kernels in k_batch.cu): for the 1-D Helmholtz
+// problems the problem table sorted by size, per-size FFT plans and twiddle pools and the
+// warp-interleaved FP64 buffers; for the 2-D problems one space each; the CUDA graph that runs
+// the whole batch as one launch; and the C ABI entry points sgm_batch_*.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -57,6 +58,23 @@ struct sgm_batch {
   double* scratch = nullptr;
   double* coef = nullptr;         // (-2 pi (k+1)(k+2), -4 pi (k+1)) per row k < Nmax
   double* mass = nullptr;         // B_kk: 3 pi / 2 for k = 0, else pi
+  // 2-D problems (sgm_batch_add_2d)
+  struct Prob2D {
+    int N, M;
+    sgm_space* sp;
+    int branch;
+  };
+  std::vector<Prob2D> p2;
+  std::vector<int64_t> off2;      // element offsets, multiples of 4
+  double a2 = 0.0, b2 = 0.0;
+  int nbranch = 0;                // graph branches used by the 2-D problems
+  // the captured graph of sgm_batch_run and the pointers it was captured with
+  cudaStream_t cs = nullptr;
+  std::vector<cudaStream_t> br;   // [0] 1-D problems, [1..] 2-D problems
+  std::vector<cudaEvent_t> ev;    // [0] fork, [1 + i] join of branch i
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  const void* cap[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 namespace {
@@ -73,6 +91,12 @@ void free_batch(sgm_batch* b) {
   cudaFree(b->scratch);
   cudaFree(b->coef);
   cudaFree(b->mass);
+  for (auto& q : b->p2) sgm_space_destroy(q.sp);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  for (cudaStream_t t : b->br) cudaStreamDestroy(t);
+  if (b->cs) cudaStreamDestroy(b->cs);
   b->magic = 0;
   delete b;
 }
@@ -237,14 +261,122 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   return SGM_OK;
 }
 
+constexpr int kBranches = 8;
+
+#define SGM_BATCH_TRY(x)           \
+  do {                             \
+    const int st_ = (x);           \
+    if (st_ != SGM_OK) return st_; \
+  } while (0)
+
+int check_batch(const sgm_batch* b) {
+  if (!b) return set_error(SGM_ERR_NULL, "batch is NULL");
+  if (b->magic != sgm_batch::kMagic) return set_error(SGM_ERR_STATE, "not a live sgm_batch");
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return set_error(SGM_ERR_STATE, "wrong current device");
+  return SGM_OK;
+}
+
+int check_pair(const void* f, const void* u, size_t bytes) {
+  if (!f || !u) return set_error(SGM_ERR_NULL, "NULL data pointer");
+  if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return set_error(SGM_ERR_ALIGN, "pointers must be 16-byte aligned");
+  const char* pa = (const char*)f;
+  const char* pb = (const char*)u;
+  if (pa < pb + bytes && pb < pa + bytes) return set_error(SGM_ERR_ALIAS, "f and u overlap");
+  return SGM_OK;
+}
+
+int launch_1d(sgm_batch* b, const void* f, void* u, cudaStream_t s) {
+  cudaError_t e = b->prec == SGM_F32
+                      ? launch_batch<float>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
+                                            b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s)
+                      : launch_batch<double>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
+                                             b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s);
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+  return SGM_OK;
+}
+
+int run_2d(sgm_batch* b, int q, const void* f2, void* u2, cudaStream_t s) {
+  const size_t el = b->prec == SGM_F32 ? 4 : 8;
+  const auto& p = b->p2[q];
+  return sgm_helmholtz(p.sp, b->a2, b->b2, (const char*)f2 + el * b->off2[q], (char*)u2 + el * b->off2[q], s);
+}
+
+// (re)capture the graph of the whole batch for these pointers
+int capture(sgm_batch* b, const void* f1, void* u1, const void* f2, void* u2) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+  std::memset(b->cap, 0, sizeof b->cap);
+  cudaError_t e = cudaSuccess;
+  auto cu = [&](cudaError_t x) {
+    if (e == cudaSuccess) e = x;
+  };
+  if (!b->cs) {
+    cu(cudaStreamCreateWithFlags(&b->cs, cudaStreamNonBlocking));
+    for (int i = 0; i <= kBranches && e == cudaSuccess; ++i) {
+      cudaStream_t t = nullptr;
+      cu(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+      if (e == cudaSuccess) b->br.push_back(t);
+    }
+    for (int i = 0; i <= kBranches + 1 && e == cudaSuccess; ++i) {
+      cudaEvent_t v = nullptr;
+      cu(cudaEventCreateWithFlags(&v, cudaEventDisableTiming));
+      if (e == cudaSuccess) b->ev.push_back(v);
+    }
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch streams: %s", cudaGetErrorString(e));
+  }
+  // one eager pass: builds every lazily created table and sets kernel attributes outside capture
+  if (b->nprob > 0) SGM_BATCH_TRY(launch_1d(b, f1, u1, b->cs));
+  for (int q = 0; q < (int)b->p2.size(); ++q) SGM_BATCH_TRY(run_2d(b, q, f2, u2, b->cs));
+  cu(cudaStreamSynchronize(b->cs));
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch warm-up: %s", cudaGetErrorString(e));
+
+  cu(cudaStreamBeginCapture(b->cs, cudaStreamCaptureModeThreadLocal));
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+  int st = SGM_OK;
+  const int nbr = 1 + b->nbranch;
+  cu(cudaEventRecord(b->ev[0], b->cs));
+  for (int i = 0; i < nbr; ++i) cu(cudaStreamWaitEvent(b->br[i], b->ev[0], 0));
+  if (e == cudaSuccess && b->nprob > 0) st = launch_1d(b, f1, u1, b->br[0]);
+  for (int q = 0; q < (int)b->p2.size() && st == SGM_OK && e == cudaSuccess; ++q)
+    st = run_2d(b, q, f2, u2, b->br[b->p2[q].branch]);
+  for (int i = 0; i < nbr; ++i) {
+    cu(cudaEventRecord(b->ev[1 + i], b->br[i]));
+    cu(cudaStreamWaitEvent(b->cs, b->ev[1 + i], 0));
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ee = cudaStreamEndCapture(b->cs, &g);
+  if (st == SGM_OK && e == cudaSuccess) e = ee;
+  if (st != SGM_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return st != SGM_OK ? st : set_error(SGM_ERR_CUDA, "batch capture: %s", cudaGetErrorString(e));
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(g);
+    b->exec = nullptr;
+    return set_error(SGM_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  b->graph = g;
+  b->cap[0] = f1;
+  b->cap[1] = u1;
+  b->cap[2] = f2;
+  b->cap[3] = u2;
+  return SGM_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double* alpha, int precision) {
-  if (!out || !n || !alpha) return set_error(SGM_ERR_NULL, "out, n and alpha must be non-NULL");
+  if (!out) return set_error(SGM_ERR_NULL, "out must be non-NULL");
   *out = nullptr;
-  if (nprob < 1) return set_error(SGM_ERR_SIZE, "nprob must be >= 1");
+  if (nprob < 0) return set_error(SGM_ERR_SIZE, "nprob must be >= 0");
+  if (nprob > 0 && (!n || !alpha)) return set_error(SGM_ERR_NULL, "n and alpha must be non-NULL");
   if (precision != SGM_F32 && precision != SGM_F64) return set_error(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
   for (int p = 0; p < nprob; ++p) {
     if (n[p] < 4 || n[p] > 4096) return set_error(SGM_ERR_SIZE, "problem %d: N = %lld outside 4..4096", p, (long long)n[p]);
@@ -289,23 +421,75 @@ int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets) {
 }
 
 int sgm_batch_helmholtz(sgm_batch* b, const void* f, void* u, void* stream) {
-  if (!b) return set_error(SGM_ERR_NULL, "batch is NULL");
+  SGM_BATCH_TRY(check_batch(b));
+  SGM_BATCH_TRY(check_pair(f, u, (b->prec == SGM_F32 ? 4 : 8) * (size_t)b->total));
+  return launch_1d(b, f, u, (cudaStream_t)stream);
+}
+
+int sgm_batch_add_2d(sgm_batch* b, int nprob, const int64_t* sizes, double a, double bc) {
+  SGM_BATCH_TRY(check_batch(b));
+  if (!sizes) return set_error(SGM_ERR_NULL, "sizes must be non-NULL");
+  if (nprob < 1) return set_error(SGM_ERR_SIZE, "nprob must be >= 1");
+  if (!b->p2.empty() || b->exec) return set_error(SGM_ERR_STATE, "2-D problems were already added or the batch has run");
+  if (!std::isfinite(a) || !std::isfinite(bc) || (a == 0.0 && bc == 0.0)) return set_error(SGM_ERR_ARG, "bad a, b");
+  for (int q = 0; q < nprob; ++q) {
+    const int64_t N = sizes[2 * q], M = sizes[2 * q + 1];
+    if (N < 4 || N > 4096 || M < 2 || M > 4096)
+      return set_error(SGM_ERR_SIZE, "2-D problem %d: sizes %lld x %lld outside [4, 4096] x [2, 4096]", q, (long long)N,
+                       (long long)M);
+  }
+  const int kinds[2] = {SGM_SHEN_DIRICHLET, SGM_FOURIER_R2C};
+  const int prec = b->prec == SGM_F32 ? (SGM_F32 | SGM_CHEB_AUTO) : SGM_F64;
+  b->off2.assign(1, 0);
+  std::vector<double> cost;
+  for (int q = 0; q < nprob; ++q) {
+    const int64_t n2[2] = {sizes[2 * q], sizes[2 * q + 1]};
+    sgm_space* sp = nullptr;
+    const int st = sgm_space_create(&sp, 2, kinds, n2, nullptr, prec);
+    if (st != SGM_OK) {
+      for (auto& r : b->p2) sgm_space_destroy(r.sp);
+      b->p2.clear();
+      b->off2.clear();
+      return st;
+    }
+    b->p2.push_back({(int)n2[0], (int)n2[1], sp, 0});
+    b->off2.push_back(b->off2.back() + (n2[0] * n2[1] + 3) / 4 * 4);
+    // the serial FP64 elimination of N/2 rows dominates a problem's time
+    cost.push_back((double)n2[0] * (64.0 + (double)n2[1] / 64.0));
+  }
+  b->a2 = a;
+  b->b2 = bc;
+  // longest processing time first over up to kBranches concurrent graph branches
+  b->nbranch = std::min(nprob, kBranches);
+  std::vector<int> order(nprob);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<double> load(b->nbranch, 0.0);
+  for (int q : order) {
+    const int i = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    b->p2[q].branch = 1 + i;
+    load[i] += cost[q];
+  }
+  return SGM_OK;
+}
+
+int sgm_batch_offsets_2d(const sgm_batch* b, int64_t* offsets) {
+  if (!b || !offsets) return set_error(SGM_ERR_NULL, "NULL argument");
   if (b->magic != sgm_batch::kMagic) return set_error(SGM_ERR_STATE, "not a live sgm_batch");
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev != b->device) return set_error(SGM_ERR_STATE, "wrong current device");
-  if (!f || !u) return set_error(SGM_ERR_NULL, "NULL data pointer");
-  const size_t bytes = (b->prec == SGM_F32 ? 4 : 8) * (size_t)b->total;
-  if (((uintptr_t)f & 15) || ((uintptr_t)u & 15)) return set_error(SGM_ERR_ALIGN, "pointers must be 16-byte aligned");
-  const char* pa = (const char*)f;
-  const char* pb = (const char*)u;
-  if (pa < pb + bytes && pb < pa + bytes) return set_error(SGM_ERR_ALIAS, "f and u overlap");
-  cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = b->prec == SGM_F32
-                      ? launch_batch<float>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
-                                            b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s)
-                      : launch_batch<double>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool,
-                                             b->wbase, b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, s);
-  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch launch: %s", cudaGetErrorString(e));
+  if (b->p2.empty()) return set_error(SGM_ERR_STATE, "the batch has no 2-D problems");
+  std::memcpy(offsets, b->off2.data(), sizeof(int64_t) * b->off2.size());
+  return SGM_OK;
+}
+
+int sgm_batch_run(sgm_batch* b, const void* f1, void* u1, const void* f2, void* u2, void* stream) {
+  SGM_BATCH_TRY(check_batch(b));
+  const size_t el = b->prec == SGM_F32 ? 4 : 8;
+  if (b->nprob > 0) SGM_BATCH_TRY(check_pair(f1, u1, el * (size_t)b->total));
+  if (!b->p2.empty()) SGM_BATCH_TRY(check_pair(f2, u2, el * (size_t)b->off2.back()));
+  const void* want[4] = {f1, u1, f2, u2};
+  if (!b->exec || std::memcmp(want, b->cap, sizeof want) != 0) SGM_BATCH_TRY(capture(b, f1, u1, f2, u2));
+  const cudaError_t e = cudaGraphLaunch(b->exec, (cudaStream_t)stream);
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
   return SGM_OK;
 }
 

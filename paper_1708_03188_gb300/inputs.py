@@ -126,3 +126,25 @@ def batch1d(nprob=4096, item=0, nmin=16, nmax=2048):
         c = g.standard_normal(N) * np.exp(-8.0 * np.arange(N) / N)
         fs.append(npcheb.chebval(cheb_points(N), c))
     return sizes, alpha, fs
+
+
+BATCH2D_SIDES = (64, 128, 256, 512, 1024)
+
+
+def batch2d(nprob=64, item=0, sides=BATCH2D_SIDES, modes=16):
+    """Sizes and physical right-hand sides of the batched 2-D problems: square N x N grids
+    (Shen-Dirichlet x R2C Fourier on [-1, 1] x [0, 2 pi)), N uniform over `sides`;
+    f = Re sum_{k, l < modes} c_kl T_k(x) exp(i l y), c_kl ~ N(0,1) + i N(0,1) times
+    exp(-(k + l) / 4)."""
+    g = rng("batch", 500 + item)
+    sizes = [(int(N), int(N)) for N in g.choice(np.asarray(sides), nprob)]
+    fs = []
+    k = np.arange(modes)
+    for N, M in sizes:
+        c = (g.standard_normal((modes, modes)) + 1j * g.standard_normal((modes, modes))) * np.exp(
+            -(k[:, None] + k[None, :]) / 4.0)
+        Tx = np.cos(np.outer(np.arccos(cheb_points(N)), k))     # T_k(x_j)
+        Ey = np.exp(1j * np.outer(k, fourier_points(M)))         # exp(i l y_m)
+        fs.append(np.real(Tx @ c @ Ey))
+    return sizes, fs
+

@@ -44,6 +44,9 @@ _SIGNATURES = {
     "sgm_batch_destroy": (ctypes.c_int, [_VP]),
     "sgm_batch_offsets": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "sgm_batch_helmholtz": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_batch_add_2d": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _D, _D]),
+    "sgm_batch_offsets_2d": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
+    "sgm_batch_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "sgm_conv3x3_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP]),
     "sgm_conv3x3_backward_data": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 5 + [_VP]),
     "sgm_conv3x3_backward_weights": (ctypes.c_int, [_VP, _VP, _VP, _VP] + [ctypes.c_int] * 6 + [_VP]),
@@ -242,22 +245,36 @@ class GinzburgLandau:
         return u_hat
 
 
-class Batch1D:
-    """Batched independent problems u_p'' - alpha_p u_p = f_p, Shen-Dirichlet basis, one grid per
-    problem (sgm_batch_*).  f and u are packed 1-D tensors; problem p occupies offsets[p]:offsets[p+1]."""
+class Batch:
+    """A batch of independent problems (sgm_batch_*): 1-D problems u_p'' - alpha_p u_p = f_p
+    (Shen-Dirichlet, one grid per problem; f and u packed, problem p at offsets[p]:offsets[p+1])
+    and optionally 2-D problems a lap(u_q) + b u_q = f_q on Shen-Dirichlet x R2C spaces (packed
+    row-major N x M arrays at offsets2d[q])."""
 
     def __init__(self, sizes, alpha, precision="f32"):
         self.sizes = [int(v) for v in sizes]
         self.precision = precision
         nprob = len(self.sizes)
-        n = (ctypes.c_int64 * nprob)(*self.sizes)
-        a = (_D * nprob)(*[float(v) for v in alpha])
+        n = (ctypes.c_int64 * max(nprob, 1))(*self.sizes)
+        a = (_D * max(nprob, 1))(*[float(v) for v in alpha])
         self._h = _VP()
         check(lib().sgm_batch_create(ctypes.byref(self._h), nprob, n, a, PRECISION[precision]))
         off = (ctypes.c_int64 * (nprob + 1))()
         check(lib().sgm_batch_offsets(self._h, off))
         self.offsets = [int(v) for v in off]
         self.dtype = torch.float32 if precision == "f32" else torch.float64
+        self.sizes2d = []
+        self.offsets2d = [0]
+
+    def add_2d(self, sizes2d, a=-1.0, b=0.0):
+        """Add 2-D problems of sizes [(N, M), ...] solving a lap(u) + b u = f."""
+        sizes2d = [(int(N), int(M)) for N, M in sizes2d]
+        flat = (ctypes.c_int64 * (2 * len(sizes2d)))(*[v for nm in sizes2d for v in nm])
+        check(lib().sgm_batch_add_2d(self._h, len(sizes2d), flat, float(a), float(b)))
+        self.sizes2d = sizes2d
+        off = (ctypes.c_int64 * (len(sizes2d) + 1))()
+        check(lib().sgm_batch_offsets_2d(self._h, off))
+        self.offsets2d = [int(v) for v in off]
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -270,16 +287,36 @@ class Batch1D:
         except Exception:
             pass
 
+    def _packed(self, t, total, what):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == self.dtype and t.numel() == total
+                and t.is_contiguous()):
+            raise ValueError(f"{what} must be a contiguous CUDA {self.dtype} tensor of {total} values")
+        return t
+
     def solve(self, f, out=None, stream=None):
+        """1-D problems only, three kernel launches (sgm_batch_helmholtz)."""
         total = self.offsets[-1]
-        if not (isinstance(f, torch.Tensor) and f.is_cuda and f.dtype == self.dtype and f.numel() == total
-                and f.is_contiguous()):
-            raise ValueError(f"f must be a contiguous CUDA {self.dtype} tensor of {total} values")
-        out = torch.empty_like(f) if out is None else out
-        if not (out.is_cuda and out.dtype == self.dtype and out.numel() == total and out.is_contiguous()):
-            raise ValueError("bad output tensor")
+        self._packed(f, total, "f")
+        out = torch.empty_like(f) if out is None else self._packed(out, total, "out")
         check(lib().sgm_batch_helmholtz(self._h, _ptr(f), _ptr(out), _stream(stream)))
         return out
+
+    def run(self, f1=None, f2=None, out1=None, out2=None, stream=None):
+        """Every problem as one CUDA graph launch (sgm_batch_run); returns (u1, u2)."""
+        p1 = p2 = (None, None)
+        if self.sizes:
+            self._packed(f1, self.offsets[-1], "f1")
+            out1 = torch.empty_like(f1) if out1 is None else self._packed(out1, self.offsets[-1], "out1")
+            p1 = (_ptr(f1), _ptr(out1))
+        if self.sizes2d:
+            self._packed(f2, self.offsets2d[-1], "f2")
+            out2 = torch.empty_like(f2) if out2 is None else self._packed(out2, self.offsets2d[-1], "out2")
+            p2 = (_ptr(f2), _ptr(out2))
+        check(lib().sgm_batch_run(self._h, *p1, *p2, _stream(stream)))
+        return out1, out2
+
+
+Batch1D = Batch
 
 
 # ---- learned-closure kernels -------------------------------------------------------------------

@@ -109,3 +109,129 @@ def test_errors():
     f = torch.zeros(36, device="cuda")
     with pytest.raises(SgmError):
         b.solve(f, out=f)
+
+
+# ---- 2-D problems and the graph-captured run of the whole batch -------------------------------
+
+def pack2d(bt, fs2, dt):
+    buf = np.zeros(bt.offsets2d[-1])
+    for q, f in enumerate(fs2):
+        buf[bt.offsets2d[q]:bt.offsets2d[q] + f.size] = np.asarray(f).ravel()
+    return torch.from_numpy(buf).to(dt).cuda()
+
+
+def unpack2d(bt, u2):
+    u = u2.cpu().double().numpy()
+    return [u[bt.offsets2d[q]:bt.offsets2d[q] + N * M].reshape(N, M) for q, (N, M) in enumerate(bt.sizes2d)]
+
+
+def oracle_2d(N, M, a, b, f):
+    sp = OSpace(["dirichlet", "r2c"], [N, M])
+    return sp.backward(sp.helmholtz(a, b, sp.scalar_product(f)))
+
+
+def tol_2d(N, M, a, b, prec):
+    if prec == "f32":
+        return 2.0 ** -15          # FP32 or BF16x3 Chebyshev axis (autotuned), FP64 eliminations
+    sp = OSpace(["dirichlet", "r2c"], [N, M])
+    mats = sp.matrices()
+    cond = max(np.linalg.cond(galerkin.helmholtz_matrix(mats, a, b, k2)) for k2 in np.ravel(sp.kappa2()))
+    return max(1e-12, 32 * EPS * cond)
+
+
+SIZES_2D = [(16, 16), (33, 20), (64, 64), (24, 128), (128, 32), (40, 7), (6, 2)]
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("a,b", [(-1.0, 0.0), (0.5, 3.0)])
+def test_graph_batch_against_oracle(prec, a, b):
+    from paper_1708_03188_gb300.sgm import Batch
+    g = np.random.default_rng(11)
+    sizes = [16, 37, 200, 1021, 5]
+    alpha = g.uniform(0, 1e4, len(sizes))
+    fs = [np.polynomial.chebyshev.chebval(inputs.cheb_points(N), g.standard_normal(N) * np.exp(-8.0 * np.arange(N) / N))
+          for N in sizes]
+    fs2 = [g.standard_normal((N, M)) for N, M in SIZES_2D]
+    bt = Batch(sizes, alpha, prec)
+    bt.add_2d(SIZES_2D, a, b)
+    dt = bt.dtype
+    f1 = torch.from_numpy(np.concatenate(fs)).to(dt).cuda()
+    f2 = pack2d(bt, fs2, dt)
+    u1, u2 = bt.run(f1, f2)
+    torch.cuda.synchronize()
+    f2w = unpack2d(bt, f2)                         # exactly the values the GPU saw
+    u2w = unpack2d(bt, u2)
+    for q, (N, M) in enumerate(SIZES_2D):
+        ref = oracle_2d(N, M, a, b, f2w[q])
+        err = np.linalg.norm(u2w[q] - ref) / np.linalg.norm(ref)
+        assert err < tol_2d(N, M, a, b, prec), (N, M, err)
+    fw = f1.cpu().double().numpy()
+    uw = u1.cpu().double().numpy()
+    for p, N in enumerate(sizes):
+        o0, o1 = bt.offsets[p], bt.offsets[p + 1]
+        ref = oracle_solve(N, alpha[p], fw[o0:o1])
+        assert np.linalg.norm(uw[o0:o1] - ref) / np.linalg.norm(ref) < (2e-5 if prec == "f32" else 1e-9), p
+
+
+def test_graph_replay_reads_current_data_and_recaptures():
+    from paper_1708_03188_gb300.sgm import Batch
+    g = np.random.default_rng(12)
+    sizes2d = [(32, 32), (64, 16), (20, 40)]
+    bt = Batch([], [], "f64")
+    bt.add_2d(sizes2d, -1.0, 0.0)
+    fa = [g.standard_normal(s) for s in sizes2d]
+    fb = [g.standard_normal(s) for s in sizes2d]
+    f2 = pack2d(bt, fa, torch.float64)
+    _, u = bt.run(None, f2)
+    torch.cuda.synchronize()
+    first = u.clone()
+    bt.run(None, f2, out2=u)                        # replay with identical pointers
+    torch.cuda.synchronize()
+    assert torch.equal(first, u)
+    f2.copy_(pack2d(bt, fb, torch.float64))         # same pointers, new values
+    bt.run(None, f2, out2=u)
+    torch.cuda.synchronize()
+    uw = unpack2d(bt, u)
+    for q, (N, M) in enumerate(sizes2d):
+        ref = oracle_2d(N, M, -1.0, 0.0, fb[q])
+        assert np.linalg.norm(uw[q] - ref) / np.linalg.norm(ref) < 1e-11
+    f2n = pack2d(bt, fa, torch.float64)             # new pointers: re-captured
+    _, un = bt.run(None, f2n)
+    torch.cuda.synchronize()
+    assert torch.equal(un, first)
+
+
+def test_workload_2d_manufactured_f32():
+    # the 64 2-D problems of the batched workload (sides 64 .. 1024) with the manufactured
+    # solution u = sin(pi x)(1 + cos 2y + sin 3y), plus the 4096 1-D problems, in one graph
+    from paper_1708_03188_gb300.sgm import Batch
+    sizes2d, _ = inputs.batch2d(64)
+    sizes, alpha, fs = inputs.batch1d(4096)
+    bt = Batch(sizes, alpha, "f32")
+    bt.add_2d(sizes2d, -1.0, 0.0)
+    f2s, exact = [], []
+    for N, M in sizes2d:
+        x, y = inputs.mesh(["dirichlet", "r2c"], (N, M))
+        f2s.append(inputs.poisson2d_f(x, y))
+        exact.append(inputs.poisson2d_u(x, y))
+    f1 = torch.from_numpy(np.concatenate(fs)).float().cuda()
+    f2 = pack2d(bt, f2s, torch.float32)
+    u1, u2 = bt.run(f1, f2)
+    torch.cuda.synchronize()
+    for q, u in enumerate(unpack2d(bt, u2)):
+        assert np.linalg.norm(u - exact[q]) / np.linalg.norm(exact[q]) < 2.0 ** -15, q
+    u1c = bt.solve(f1)                              # the same 1-D kernels without the graph
+    torch.cuda.synchronize()
+    assert torch.equal(u1, u1c)
+
+
+def test_batch_2d_errors():
+    from paper_1708_03188_gb300.sgm import Batch, SgmError
+    bt = Batch([16], [1.0], "f32")
+    with pytest.raises(SgmError):
+        bt.add_2d([(3, 16)])                        # N < 4
+    bt.add_2d([(16, 16)])
+    with pytest.raises(SgmError):
+        bt.add_2d([(16, 16)])                       # only once
+    with pytest.raises(ValueError):
+        bt.run(torch.zeros(16, device="cuda"), None)
