@@ -258,7 +258,7 @@ int sgm_batch_offsets_2d(const sgm_batch* batch, int64_t* offsets);
  * CUDA graph launch on `stream`.  The first call, and any call whose four pointers differ from
  * those of the captured graph, runs each problem once eagerly (so that every lazily built
  * table exists), then captures the graph on internal streams: the 1-D kernels on one branch and
- * the 2-D problems spread over up to 8 concurrent branches, longest first; that call
+ * the 2-D problems spread over up to 64 concurrent branches, longest first; that call
  * synchronises the device.  Later calls only launch the graph (asynchronous).  f1/u1 may be NULL
  * when the batch has no 1-D problems, f2/u2 when it has no 2-D problems.  Calls on one batch
  * must not overlap.

@@ -261,7 +261,7 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   return SGM_OK;
 }
 
-constexpr int kBranches = 8;
+constexpr int kBranches = 64;
 
 #define SGM_BATCH_TRY(x)           \
   do {                             \
