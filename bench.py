@@ -463,33 +463,67 @@ def closure_measure(stream, iters=1500):
     train_ms = a.elapsed_time(b)
     e1p, e1l = closure.relative_errors(coarse, net, test_snaps, scale, horizon=1)
     e4p, e4l = closure.relative_errors(coarse, net, test_snaps, scale, horizon=4)
-    # cost of one corrected coarse step (batch 1) vs the 5 fine steps of the same 0.05
-    u = test_snaps[0, :1].contiguous()
 
-    def timed(fn, reps=20):
-        fn()
+    # Cost per state of advancing B states by one coarse step (0.05 time units), every path
+    # captured as a CUDA graph over the same batch: the corrected coarse step, the plain coarse
+    # step, plain steps on finer grids (their one-step error against the truncated fine run
+    # shows the resolution a plain run needs to match the learned error), and the 256^2 fine run
+    # itself in complex64 and in the all-FP64 form (complex128) - five 0.01 steps each.
+    B = 32
+    states = test_snaps[:, :-1].reshape(-1, 32, 32)[:B].contiguous()
+
+    def per_state_ms(replay, reps=10):
+        replay()
         torch.cuda.synchronize()
         a.record(stream)
         for _ in range(reps):
-            fn()
+            replay()
         b.record(stream)
         b.synchronize()
-        return a.elapsed_time(b) / reps
+        return a.elapsed_time(b) / reps / B
 
-    corr_ms = timed(lambda: closure.corrected_step(coarse, net, u, scale))
-    plain_ms = timed(lambda: coarse.step_batch(u))
+    u_c = states.clone()
+    out_c = torch.empty_like(u_c)
+
+    def corrected():
+        out_c.copy_(closure.corrected_step(coarse, net, u_c, scale))
+
+    def plain_step(model, u):
+        def run():
+            for i in range(u.shape[0]):
+                model.gl.step(u[i], 1)
+        return run
+
+    cost = {"coarse_learned_32": per_state_ms(closure.graphed(corrected)),
+            "coarse_plain_32": per_state_ms(closure.graphed(plain_step(coarse, states.clone())))}
     from paper_1708_03188_gb300.sgm import GinzburgLandau, Space
-    spf = Space(["c2c", "c2c"], (256, 256), domain=closure.DOMAIN, precision="f32")
-    glf = GinzburgLandau(spf, 1.5, -0.5, 0.01, "ifrk4")
-    uf = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
-    fine_ms = timed(lambda: glf.step(uf, 5))
+    matched = {}
+    for Mc in (64,):
+        snaps_m = closure.fine_trajectories(256, Mc, 2, 30.0, 20, 0.01, 0.05, first_item=100)
+        cm = closure.CoarseModel(Mc, 0.05)
+        start = snaps_m[:, :-1].reshape(-1, Mc, Mc)
+        truth = snaps_m[:, 1:].reshape(-1, Mc, Mc)
+        stepped = cm.step_batch(start)
+        err = torch.linalg.vector_norm((stepped - truth).reshape(truth.shape[0], -1), dim=1) / \
+            torch.linalg.vector_norm(truth.reshape(truth.shape[0], -1), dim=1)
+        matched[f"plain_{Mc}"] = float(err.mean())
+        cost[f"coarse_plain_{Mc}"] = per_state_ms(closure.graphed(plain_step(cm, start[:B].contiguous())))
+    for prec, dt in (("f32", torch.complex64), ("f64", torch.complex128)):
+        spf = Space(["c2c", "c2c"], (256, 256), domain=closure.DOMAIN, precision=prec)
+        glf = GinzburgLandau(spf, 1.5, -0.5, 0.01, "ifrk4")
+        uf = torch.zeros((B, 256, 256), dtype=dt, device="cuda")
+
+        def fine(glf=glf, uf=uf):
+            for i in range(B):
+                glf.step(uf[i], 5)
+        cost[f"fine_plain_256_{prec}"] = per_state_ms(closure.graphed(fine))
     return {"fine": "256^2, IF-RK4 dt 0.01", "coarse": "32^2, IF-RK4 dt 0.05", "params": net.num_params,
             "train": {"iters": iters, "batch": 32, "ms_per_iter": round(train_ms / iters, 4),
                       "loss_first_last": [round(hist[0], 4), round(hist[-1], 4)]},
-            "one_step_rel_error": {"plain": e1p, "learned": e1l},
+            "one_step_rel_error": {"plain": e1p, "learned": e1l, **matched},
             "four_step_rel_error": {"plain": e4p, "learned": e4l},
-            "ms_per_0.05": {"coarse_plain": round(plain_ms, 4), "coarse_learned": round(corr_ms, 4),
-                            "fine_plain": round(fine_ms, 4)},
+            "ms_per_state_per_0.05": {k: round(v, 5) for k, v in cost.items()},
+            "timing": f"each path one CUDA graph over a batch of {B} states; ms per state per 0.05 time units",
             "wall_s": round(_time.time() - t0, 1)}
 
 

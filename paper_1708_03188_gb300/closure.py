@@ -95,11 +95,12 @@ class ClosureNet:
 
 
 class CoarseModel:
-    """Coarse Ginzburg-Landau stepper (complex64, integrating-factor RK4) and its transforms."""
+    """Ginzburg-Landau stepper (integrating-factor RK4; complex64, or complex128 with
+    precision="f64") and its transforms."""
 
-    def __init__(self, M, dt, beta=1.5, gamma=-0.5):
+    def __init__(self, M, dt, beta=1.5, gamma=-0.5, precision="f32"):
         self.M = M
-        self.space = sgm.Space(["c2c", "c2c"], (M, M), domain=DOMAIN, precision="f32")
+        self.space = sgm.Space(["c2c", "c2c"], (M, M), domain=DOMAIN, precision=precision)
         self.gl = sgm.GinzburgLandau(self.space, beta, gamma, dt, "ifrk4")
 
     def step_batch(self, uh):
@@ -225,3 +226,19 @@ def relative_errors(coarse, net, snaps, scale_t, horizon=1):
     ep = torch.linalg.vector_norm((plain - truth).reshape(truth.shape[0], -1), dim=1) / tn
     el = torch.linalg.vector_norm((learned - truth).reshape(truth.shape[0], -1), dim=1) / tn
     return float(ep.mean()), float(el.mean())
+
+
+def graphed(fn):
+    """Capture fn() - device work on the current stream into buffers that stay fixed - into a
+    CUDA graph after one eager warm-up run; returns a function that replays the graph."""
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        fn()
+    return g.replay
+
