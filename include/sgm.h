@@ -124,7 +124,8 @@ int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out);
 /* Chebyshev-axis method in use: *method = 0 (DCT via FFT), 1 (tensor-core contraction). */
 int sgm_space_cheb_method(const sgm_space* space, int* method);
 /*
- * Number of bounded waits inside tensor-core kernels on the current device that gave up
+ * Number of bounded waits inside tensor-core kernels (Chebyshev contraction, 32 -> 32 convolution
+ * layers) on the current device that gave up
  * (each wait gives up after ~1 s; the kernel then skips its result and returns).  Reads a
  * device counter synchronously; reset != 0 also zeroes it.  A non-zero count means the
  * results of those launches are invalid.

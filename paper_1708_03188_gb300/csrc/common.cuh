@@ -117,6 +117,7 @@ int tc_pad16(int n);
 // number of uint16 in the image is 2 * tc_pad16(N)^2
 std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N);
 int tc_timeouts(bool reset);
+int cnn_tc_timeouts(bool reset);   // k_cnn_tc.cu
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out,

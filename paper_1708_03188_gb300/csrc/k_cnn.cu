@@ -6,7 +6,9 @@
 // One layer is the circular cross-correlation
 //     y[b, o, i, j] = bias[o] + sum_{c, p, q} W[o, c, p, q] x[b, c, (i + p - 1) mod H, (j + q - 1) mod W]
 // (p, q in 0..2), optionally followed by ReLU.  Activations and weights are stored in BF16,
-// every product is accumulated in FP32; gradients are FP32.  A CTA owns a 16 x 16 pixel
+// every product is accumulated in FP32; gradients are FP32.  The 32 -> 32 layers run as
+// implicit GEMMs on the tensor cores (k_cnn_tc.cu); the 2 -> 32 and 32 -> 2 layers, whose GEMM
+// has 2 rows or a K of 18, use the kernels below on the CUDA cores.  A CTA owns a 16 x 16 pixel
 // tile of one sample: it stages the tile plus a one-pixel periodic halo of every input channel
 // and the layer's weights in shared memory (FP32), and each thread accumulates all output
 // channels of one pixel (forward and input gradient) or a few (output, input) channel pairs over
@@ -20,6 +22,15 @@
 #include "common.cuh"
 
 namespace sgm {
+
+// the 32 -> 32 layers on the tensor cores (k_cnn_tc.cu)
+template <typename TO>
+cudaError_t launch_conv_tc_fwd(const __nv_bfloat16* x, const __nv_bfloat16* w, const float* bias, TO* y, int B, int H,
+                               int W, bool relu, cudaStream_t s);
+cudaError_t launch_conv_tc_bwd_data(const float* gy, const __nv_bfloat16* w, const __nv_bfloat16* mask, float* gx,
+                                    int B, int H, int W, cudaStream_t s);
+cudaError_t launch_conv_tc_wgrad(const float* gy, const __nv_bfloat16* x, float* gw, float* gb, int B, int H, int W,
+                                 cudaStream_t s);
 
 constexpr int kTile = 16;
 constexpr int kHalo = kTile + 2;
@@ -281,8 +292,13 @@ int sgm_conv3x3_forward(const void* x, const void* w, const float* bias, void* y
       with_out((const bf*)x);
     }
   };
+  if (Cin == 32 && Cout == 32) {
+    const cudaError_t e = out_f32 ? launch_conv_tc_fwd<float>((const bf*)x, wb, bias, (float*)y, B, H, W, relu, s)
+                                  : launch_conv_tc_fwd<bf>((const bf*)x, wb, bias, (bf*)y, B, H, W, relu, s);
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "conv forward: %s", cudaGetErrorString(e));
+    return SGM_OK;
+  }
   if (Cin == 2) pick(std::integral_constant<int, 2>{}, std::integral_constant<int, 32>{});
-  else if (Cout == 32) pick(std::integral_constant<int, 32>{}, std::integral_constant<int, 32>{});
   else pick(std::integral_constant<int, 32>{}, std::integral_constant<int, 2>{});
   return launched("conv forward");
 }
@@ -301,8 +317,12 @@ int sgm_conv3x3_backward_data(const float* gy, const void* w, const void* mask, 
     if (launch_smem(kernel, sb, grid, s) != SGM_OK) return;
     kernel<<<grid, 256, sb, s>>>(gy, wb, mb, gx, H, W);
   };
+  if (Cin == 32 && Cout == 32) {
+    const cudaError_t e = launch_conv_tc_bwd_data(gy, wb, mb, gx, B, H, W, s);
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "conv backward data: %s", cudaGetErrorString(e));
+    return SGM_OK;
+  }
   if (Cin == 2) go(k_conv_bwd_data<2, 32>);
-  else if (Cout == 32) go(k_conv_bwd_data<32, 32>);
   else go(k_conv_bwd_data<32, 2>);
   return launched("conv backward data");
 }
@@ -326,7 +346,9 @@ int sgm_conv3x3_backward_weights(const float* gy, const void* x, float* gw, floa
     if (in_f32) go(k_conv_bwd_weights<2, 32, float>, (const float*)x);
     else go(k_conv_bwd_weights<2, 32, bf>, (const bf*)x);
   } else if (Cout == 32) {
-    go(k_conv_bwd_weights<32, 32, bf>, (const bf*)x);
+    const cudaError_t e = launch_conv_tc_wgrad(gy, (const bf*)x, gw, gb, B, H, W, s);
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "conv backward weights: %s", cudaGetErrorString(e));
+    return SGM_OK;
   } else {
     go(k_conv_bwd_weights<32, 2, bf>, (const bf*)x);
   }

@@ -658,9 +658,9 @@ int sgm_space_cheb_method(const sgm_space* space, int* method) {
 
 int sgm_tc_wait_timeouts(int* count, int reset) {
   if (!count) return fail(SGM_ERR_NULL, "NULL argument");
-  const int v = tc_timeouts(reset != 0);
-  if (v < 0) return fail(SGM_ERR_CUDA, "reading the device wait counter failed");
-  *count = v;
+  const int v = tc_timeouts(reset != 0), w = cnn_tc_timeouts(reset != 0);
+  if (v < 0 || w < 0) return fail(SGM_ERR_CUDA, "reading the device wait counters failed");
+  *count = v + w;
   return SGM_OK;
 }
 
