@@ -91,47 +91,70 @@ __global__ void __launch_bounds__(256) k_conv_tc(const void* __restrict__ in, co
     *reinterpret_cast<uint4*>(Bs + cm_off(n, kg * 8, kLboN32)) =
         make_uint4(pk(v[0], v[1]), pk(v[2], v[3]), pk(v[4], v[5]), pk(v[6], v[7]));
   }
-  // A operand: row m = pixel, k = 9 c + t: the input channel c at the pixel shifted by tap t
-  for (int e = tid; e < kPix * kC; e += 256) {
-    const int m = e & (kPix - 1), c = e >> 7;
-    const long rem = r0 + m;
-    const int i = (int)(rem / W), j = (int)(rem - (long)i * W);
-    const long cbase = (b * kC + c) * plane;
+  // A operand: row m = pixel, k = 9 c + t: the input channel c at the pixel shifted by tap t.
+  // One item = 8 consecutive k of one pixel (a 16-byte core-matrix row); a warp takes 32
+  // consecutive pixels, so its gathers are coalesced and its stores fill 512 contiguous bytes.
+  // The input gradient stages K in two halves through the same buffer (hi and lo parts of 144
+  // columns each), which keeps the CTA at 92 KB of shared memory, two CTAs per SM.
+  constexpr int NHALF = MODE == 0 ? 1 : 2, KGH = kKG / NHALF;
+  const uint32_t part_bytes = (uint32_t)kPix * KGH * 16;
+  bool ok = true;
+  uint32_t tmem = 0;
+  for (int hf = 0; hf < NHALF; ++hf) {
+    for (int e = tid; e < kPix * KGH; e += 256) {
+      const int m = e & (kPix - 1), kgl = e >> 7, kg = hf * KGH + kgl;
+      const long rem = r0 + m;
+      const int i = (int)(rem / W), j = (int)(rem - (long)i * W);
+      // wrapped neighbour rows (as element offsets) and columns of the pixel
+      const int im = i == 0 ? H - 1 : i - 1, ip = i == H - 1 ? 0 : i + 1;
+      const int jm = j == 0 ? W - 1 : j - 1, jp = j == W - 1 ? 0 : j + 1;
+      const long row0 = (long)im * W, row1 = (long)i * W, row2 = (long)ip * W;
+      int c = (kg * 8) / 9, t = kg * 8 - 9 * c;
+      uint16_t h[8], l[8];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int ii = (i + t / 3 - 1 + H) % H, jj = (j + t % 3 - 1 + W) % W;
-      const uint32_t off = cm_off(m, c * 9 + t, kLboM128);
-      if constexpr (MODE == 0) {
-        const __nv_bfloat16 v = reinterpret_cast<const __nv_bfloat16*>(in)[cbase + (long)ii * W + jj];
-        *reinterpret_cast<uint16_t*>(As + off) = bits(v);
-      } else {
-        const float v = reinterpret_cast<const float*>(in)[cbase + (long)ii * W + jj];
-        uint16_t h, l;
-        tc::split_bf16(v, h, l);
-        *reinterpret_cast<uint16_t*>(As + off) = h;
-        *reinterpret_cast<uint16_t*>(As + kABytes + off) = l;
+      for (int r = 0; r < 8; ++r) {
+        const int p = t >= 6 ? 2 : (t >= 3 ? 1 : 0), q = t - 3 * p;
+        const long g = (b * kC + c) * plane + (p == 0 ? row0 : (p == 1 ? row1 : row2)) + (q == 0 ? jm : (q == 1 ? j : jp));
+        if constexpr (MODE == 0) {
+          h[r] = bits(reinterpret_cast<const __nv_bfloat16*>(in)[g]);
+        } else {
+          tc::split_bf16(reinterpret_cast<const float*>(in)[g], h[r], l[r]);
+        }
+        if (++t == 9) {
+          t = 0;
+          ++c;
+        }
       }
+      const uint32_t off = cm_off(m, kgl * 8, kLboM128);
+      *reinterpret_cast<uint4*>(As + off) = make_uint4(pk(h[0], h[1]), pk(h[2], h[3]), pk(h[4], h[5]), pk(h[6], h[7]));
+      if constexpr (MODE == 1)
+        *reinterpret_cast<uint4*>(As + part_bytes + off) =
+            make_uint4(pk(l[0], l[1]), pk(l[2], l[3]), pk(l[4], l[5]), pk(l[6], l[7]));
     }
-  }
-  tc::fence_proxy_async();
-  tc::fence_before_sync();
-  __syncthreads();
-  tc::fence_after_sync();
-  const uint32_t tmem = tmem_slot;
-  if (tid == 0) {
-    const uint32_t idesc = tc::idesc_bf16(kPix, kC);
-    const uint32_t a0 = tc::smem_addr(As), bb = tc::smem_addr(Bs);
-    for (int s = 0; s < kK / 16; ++s) {
-      const uint64_t db = tc::smem_desc(bb + (uint32_t)s * 2 * kLboN32, kLboN32, 128);
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    tmem = tmem_slot;
+    if (tid == 0) {
+      const uint32_t idesc = tc::idesc_bf16(kPix, kC);
+      const uint32_t a0 = tc::smem_addr(As), bb = tc::smem_addr(Bs);
+      for (int s = 0; s < KGH / 2; ++s) {
+        const int sg = hf * (KGH / 2) + s;   // K step within the full 288
+        const uint64_t db = tc::smem_desc(bb + (uint32_t)sg * 2 * kLboN32, kLboN32, 128);
 #pragma unroll
-      for (int part = 0; part < NPART; ++part) {
-        const uint64_t da = tc::smem_desc(a0 + (uint32_t)part * kABytes + (uint32_t)s * 2 * kLboM128, kLboM128, 128);
-        tc::mma_bf16(tmem, da, db, idesc, (s > 0 || part > 0) ? 1u : 0u);
+        for (int part = 0; part < (MODE == 0 ? 1 : 2); ++part) {
+          const uint64_t da = tc::smem_desc(a0 + (uint32_t)part * part_bytes + (uint32_t)s * 2 * kLboM128, kLboM128, 128);
+          tc::mma_bf16(tmem, da, db, idesc, (sg > 0 || part > 0) ? 1u : 0u);
+        }
       }
+      tc::mma_commit(&bar);
     }
-    tc::mma_commit(&bar);
+    // the next half overwrites the A operand: wait for these MMAs first
+    ok = wait_mma(&bar, (uint32_t)hf) && ok;
+    tc::fence_before_sync();
   }
-  if (wait_mma(&bar, 0)) {
+  if (ok) {
     const int lq = warp & 3, n0 = (warp >> 2) * 16;
     const int m = lq * 32 + (tid & 31);
     float v[16];
@@ -159,7 +182,7 @@ __global__ void __launch_bounds__(256) k_conv_tc(const void* __restrict__ in, co
 }
 
 constexpr int kWChunk = 64;            // pixels per MMA chunk of the weight gradient
-constexpr int kWChunksPerCta = 8;      // 512 pixels per CTA
+constexpr int kWChunksPerCta = 2;      // 128 pixels per CTA: enough CTAs to fill the SMs
 constexpr uint32_t kWA = kPix * kWChunk * 2;   // 16 KB: 128 (c, t) rows x 64 pixels
 constexpr uint32_t kWB = kC * kWChunk * 2;     // 4 KB: 32 channels x 64 pixels, one part
 
@@ -201,14 +224,18 @@ __global__ void __launch_bounds__(256) k_conv_tc_wgrad(const float* __restrict__
       const int mm = mt * kPix + m;
       uint16_t v[8];
       if (mm < kK) {
-        const int c = mm / 9, t = mm - 9 * c;
-        const long cbase = (b * kC + c) * plane;
+        // 8 consecutive pixels of one row (W is a multiple of 16), shifted by tap t
+        const int c = mm / 9, t = mm - 9 * c, p = t / 3, q = t - 3 * p;
+        const long rem = r0 + kg * 8;
+        const int i = (int)(rem / W), j0 = (int)(rem - (long)i * W);
+        int ii = i + p - 1;
+        ii = ii < 0 ? ii + H : (ii >= H ? ii - H : ii);
+        const __nv_bfloat16* row = x + (b * kC + c) * plane + (long)ii * W;
 #pragma unroll
         for (int r = 0; r < 8; ++r) {
-          const long rem = r0 + kg * 8 + r;
-          const int i = (int)(rem / W), j = (int)(rem - (long)i * W);
-          const int ii = (i + t / 3 - 1 + H) % H, jj = (j + t % 3 - 1 + W) % W;
-          v[r] = bits(x[cbase + (long)ii * W + jj]);
+          int jj = j0 + r + q - 1;
+          jj = jj < 0 ? jj + W : (jj >= W ? jj - W : jj);
+          v[r] = bits(row[jj]);
         }
       } else {
 #pragma unroll
@@ -270,7 +297,7 @@ __global__ void __launch_bounds__(256) k_conv_tc_wgrad(const float* __restrict__
 
 }  // namespace
 
-size_t conv_tc_smem(int mode) { return kBBytes + (mode == 0 ? 1 : 2) * kABytes; }
+size_t conv_tc_smem(int /*mode*/) { return kBBytes + kABytes; }   // 92 KB: the A buffer holds 288 (or 2 x 144) columns
 
 // forward of a 32 -> 32 layer; H * W must be a multiple of 128
 template <typename TO>
