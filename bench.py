@@ -158,7 +158,13 @@ def hbm_peak():
 #   biharmonic (53 per row of the shared factorisation) / 4 + 34 per right-hand-side column = 47.25
 # (row assembly from the coefficient tables, elimination of the sub-diagonal entries, one
 # reciprocal = approximation + cubic Newton step, back substitution with the tail sums).
-FLOPS_PER_ROW = {"dirichlet": 19.75, "biharmonic": 47.25}
+# algorithmic FP64 flops per row per Fourier column of one elimination: the factorisation (15
+# Dirichlet, 53 biharmonic) shared by the columns of one thread (2 Dirichlet, 4 biharmonic on the
+# square box) plus the per-column right-hand-side work (16 and 34)
+FLOPS_PER_ROW = {"dirichlet": 15 / 2 + 16, "biharmonic": 53 / 4 + 34}
+# DRAM bytes (read + write) of one k_solve_biharmonic<double, 4> launch on the 256^3 box, from
+# ncu (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_solve_biharmonic_box3d_256.md)
+BIH_TRAFFIC_BYTES = 309_025_280 + 318_420_736
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
 
 
@@ -278,7 +284,8 @@ def run_ours(args):
     achieved = fl_b / t_b / 1e12
     roofline = {"kernel": "k_solve_biharmonic<double,4> (FP64 elimination, 33024 columns x 252 rows)",
                 "bound": "alu", "achieved": round(achieved, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": None,
+                "frac": round(achieved / FP64_PEAK_TFLOPS, 4), "traffic": BIH_TRAFFIC_BYTES,
+                "traffic_unit": "bytes per launch (ncu DRAM read + write)",
                 "peak_source": "GB300 nominal FP64 1.25 TFLOP/s (FMA probe measured 1.19)",
                 "dirichlet_solve_tflops": round(fl_p / (br["poisson_solve_kernel_ms"] * 1e-3) / 1e12, 4)}
 

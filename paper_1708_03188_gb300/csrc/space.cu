@@ -606,7 +606,11 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       if (ndim == 3) {
         const double L1 = s->dom[3] - s->dom[2], L2 = s->dom[5] - s->dom[4];
         const bool square = kinds[2] == SGM_FOURIER_R2C && n[1] == n[2] && std::fabs(L1 - L2) <= 1e-12 * std::fabs(L1);
-        if (square) {
+        // Four columns per factorisation leave one warp per SM sub-partition on a 256^3 box, too
+        // few to hide the latency of dependent FP64 instructions; the Dirichlet elimination, whose
+        // per-column work is small next to its factorisation, runs faster with pairs and twice the
+        // warps.  The biharmonic elimination keeps the groups of four.
+        if (square && kinds[0] == SGM_SHEN_BIHARMONIC) {
           // columns (+-a, b), (+-b, a) share kappa2: one elimination thread per (a, b), a <= b
           const int M = (int)n[1], h = M / 2;
           std::vector<int2> g;
