@@ -227,6 +227,240 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
   }
 }
 
+// Two-sided elimination of the Dirichlet systems (used with NC = 1: 1-D and 2-D spaces).
+// A CTA of four warps owns 32 work items: warps (p, side) with p the parity and side 0 / 1.
+// Side 0 eliminates rows 0 .. h-1 top-down as k_solve_dirichlet does (h = ceil(n / 2)); side 1
+// runs rows n-1 .. h bottom-up, writing each unknown and the tail sum T_i = sum_{j>=i} u_j as
+// affine functions of the unknown above:
+//     u_i = a_i + b_i u_{i-1},   T_i = A_i + B_i u_{i-1},
+//     D_i = d_i + ell b_{i+1} + g_i B_{i+1},   a_i = (f_i - ell a_{i+1} - g_i A_{i+1}) / D_i,
+//     b_i = -ell / D_i,   A_i = A_{i+1} + (1 + B_{i+1}) a_i,   B_i = (1 + B_{i+1}) b_i,
+// from a_n = b_n = A_n = B_n = 0 (row i of the system: ell u_{i-1} + d_i u_i + ell u_{i+1} +
+// g_i T_{i+1} = f_i).  For a = 0 (no ell terms) this is the ordinary back substitution of the
+// upper-triangular stiffness rows; with a mass term |b_i| stays below one and B_i bounded.  The
+// sides meet through shared memory at the reduced top row h-1,
+//     u_{h-1} = (f'_{h-1} - ell a_h - g'_{h-1} A_h) / (d'_{h-1} + ell b_h + g'_{h-1} B_h),
+// after which side 0 back-substitutes rows h-2 .. 0 and side 1 forward-substitutes rows h .. n-1.
+// Each serial chain is half as long as in the one-sided kernel and twice as many warps run it.
+template <typename T, int NC>
+__global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict__ in, void* __restrict__ out, int N,
+                                                          long ncols, int real, double a, double b,
+                                                          const __grid_constant__ Wavenumbers wn,
+                                                          const __grid_constant__ ColumnMap cm,
+                                                          const double* __restrict__ tab, int ts,
+                                                          double* __restrict__ scratch) {
+  extern __shared__ double sh[];
+  double* aA0 = sh;        // a * A0_k
+  double* aG = sh + ts;    // a * G_k
+  constexpr int XV = 6 * NC + 2;                     // exchange values per (parity, lane)
+  double* xch = sh + 2 * ts;                         // [parity][lane][XV]
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    aA0[k] = a * tab[TD_A0 * ts + k];
+    aG[k] = a * tab[TD_G * ts + k];
+  }
+  __syncthreads();
+  constexpr int NV = 2 + 2 * NC;
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = warp & 1, side = warp >> 1;
+  const long nwb = (cm.nitems + 31) / 32;
+  const int nb = N - 2;
+  const int n = (nb - p + 1) / 2, h = (n + 1) / 2;
+  const double half_pi = 1.5707963267948966;
+  const long rstep = 2 * ncols;
+  const long sstep = (long)NV * nth;
+  double* x = xch + (p * 32 + lane) * XV;
+  for (long grp = blockIdx.x; grp < nwb; grp += gridDim.x) {
+    const long item = grp * 32 + lane;
+    const bool valid = item < cm.nitems;
+    long cc[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) cc[q] = 0;
+    if (valid) map_columns<NC>(cm, item, cc);
+    const double k2 = valid ? kappa2_of(wn, cc[0]) : 0.0;
+    const double aB = b - a * k2;
+    const double ell = -aB * half_pi;
+    const double aBpi = aB * 3.141592653589793;   // aB * B0_k for k > 0
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    double* s = scratch + gt;
+    // reduced top row h-1 (side 0)
+    double dl = 1.0, gl = 0.0;
+    double2 fl[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) fl[q] = make_double2(0.0, 0.0);
+    if (side == 0) {
+      double pr = 0.0, pge = 0.0, pg = 0.0;
+      double2 pf[NC], fn[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        pf[q] = make_double2(0.0, 0.0);
+        fn[q] = (valid && h > 0) ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+      }
+      for (int i = 0; i < h; ++i) {
+        const int k = p + 2 * i;
+        double2 f[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f[q] = fn[q];
+          if (valid && i + 1 < h) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+        }
+        double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
+        double g = aG[k];
+        if (i > 0) {
+          const double mu = ell * pr;
+          d = fma(-mu, pge, d);
+          g = fma(-mu, pg, g);
+#pragma unroll
+          for (int q = 0; q < NC; ++q) {
+            f[q].x = fma(-mu, pf[q].x, f[q].x);
+            f[q].y = fma(-mu, pf[q].y, f[q].y);
+          }
+        }
+        const double r = rcp64(d);
+        s[0] = r;
+        s[nth] = g;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          s[(2 + 2 * q) * nth] = f[q].x;
+          s[(3 + 2 * q) * nth] = f[q].y;
+          pf[q] = f[q];
+        }
+        s += sstep;
+        pr = r; pg = g; pge = g + ell;
+        dl = d; gl = g;
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) fl[q] = pf[q];
+    } else {
+      double bn = 0.0, Bn = 0.0;
+      double2 an[NC], An[NC], fn[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        an[q] = An[q] = make_double2(0.0, 0.0);
+        fn[q] = (valid && n > h) ? ld2<T>(in, off[q] + (long)(n - 1) * rstep, real) : make_double2(0.0, 0.0);
+      }
+      for (int i = n - 1; i >= h; --i) {
+        const int k = p + 2 * i;
+        double2 f[NC];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f[q] = fn[q];
+          if (valid && i - 1 >= h) fn[q] = ld2<T>(in, off[q] + (long)(i - 1) * rstep, real);
+        }
+        const double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
+        const double g = aG[k];
+        const double R = rcp64(fma(g, Bn, fma(ell, bn, d)));
+        const double bi = -ell * R, onep = 1.0 + Bn;
+        s[0] = bi;
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          double2 ai;
+          ai.x = fma(-g, An[q].x, fma(-ell, an[q].x, f[q].x)) * R;
+          ai.y = fma(-g, An[q].y, fma(-ell, an[q].y, f[q].y)) * R;
+          An[q].x = fma(onep, ai.x, An[q].x);
+          An[q].y = fma(onep, ai.y, An[q].y);
+          an[q] = ai;
+          s[(1 + 2 * q) * nth] = ai.x;
+          s[(2 + 2 * q) * nth] = ai.y;
+        }
+        s += sstep;
+        bn = bi;
+        Bn = onep * bi;
+      }
+      // hand (a_h, b_h, A_h, B_h) to side 0
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        x[4 * q] = an[q].x;
+        x[4 * q + 1] = an[q].y;
+        x[4 * q + 2] = An[q].x;
+        x[4 * q + 3] = An[q].y;
+      }
+      x[4 * NC] = bn;
+      x[4 * NC + 1] = Bn;
+    }
+    __syncthreads();
+    if (side == 0) {
+      double2 un[NC], Ts[NC];
+      if (h > 0) {
+        const double bh = x[4 * NC], Bh = x[4 * NC + 1];
+        const double rd = rcp64(fma(gl, Bh, fma(ell, bh, dl)));
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          const double2 ah = make_double2(x[4 * q], x[4 * q + 1]), Ah = make_double2(x[4 * q + 2], x[4 * q + 3]);
+          double2 u;
+          u.x = fma(-gl, Ah.x, fma(-ell, ah.x, fl[q].x)) * rd;
+          u.y = fma(-gl, Ah.y, fma(-ell, ah.y, fl[q].y)) * rd;
+          x[4 * NC + 2 + 2 * q] = u.x;           // u_{h-1} for side 1
+          x[4 * NC + 3 + 2 * q] = u.y;
+          // u_h = a_h + b_h u_{h-1},  T_h = A_h + B_h u_{h-1}
+          un[q] = u;
+          Ts[q] = make_double2(fma(Bh, u.x, Ah.x), fma(Bh, u.y, Ah.y));
+          if (valid) st2<T>(out, off[q] + (long)(h - 1) * rstep, real, u);
+        }
+      }
+      // back substitution of rows h-2 .. 0 (Ts = T_{i+1} after adding u_{i+1})
+      double vn[NV];
+      if (h > 1) {
+        s -= 2 * sstep;   // row h-2 (s was one past row h-1)
+#pragma unroll
+        for (int v = 0; v < NV; ++v) vn[v] = s[v * nth];
+      }
+      for (int i = h - 2; i >= 0; --i) {
+        double v[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) v[j] = vn[j];
+        if (i > 0) {
+          s -= sstep;
+#pragma unroll
+          for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
+        }
+        const double r = v[0], g = v[1];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          Ts[q].x += un[q].x;
+          Ts[q].y += un[q].y;
+          double2 u;
+          u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
+          u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
+          if (valid) st2<T>(out, off[q] + (long)i * rstep, real, u);
+          un[q] = u;
+        }
+      }
+      if (valid)
+        for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+          for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+        }
+    }
+    __syncthreads();
+    if (side == 1) {
+      // forward substitution of rows h .. n-1 from u_{h-1}
+      double2 up[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q)
+        up[q] = h > 0 ? make_double2(x[4 * NC + 2 + 2 * q], x[4 * NC + 3 + 2 * q]) : make_double2(0.0, 0.0);
+      // side 1 wrote rows n-1 .. h at scratch slots 0 .. n-1-h; row i is slot n-1-i
+      double* base = scratch + gt;
+      for (int i = h; i < n; ++i) {
+        const double* sr = base + (long)(n - 1 - i) * sstep;
+        const double bi = sr[0];
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          double2 u;
+          u.x = fma(bi, up[q].x, sr[(1 + 2 * q) * nth]);
+          u.y = fma(bi, up[q].y, sr[(2 + 2 * q) * nth]);
+          if (valid) st2<T>(out, off[q] + (long)i * rstep, real, u);
+          up[q] = u;
+        }
+      }
+    }
+    __syncthreads();   // the exchange slots are reused by the next group
+  }
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict__ in, void* __restrict__ out,
                                                           int N, long ncols, int real, double a, double b,
@@ -399,7 +633,25 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
   const unsigned grid = (unsigned)(threads / 128);
   const int ts = N + 8;
   cudaError_t e;
-  if (basis == kDirichlet) {
+  if (basis == kDirichlet && NC == 1) {
+    // two-sided kernel for the one-column-per-thread spaces (1-D and 2-D, few columns, long
+    // serial chains); the 3-D box keeps the one-sided kernel, whose pairs already fill the GPU.
+    // Four warps per 32 work items, each thread at most ceil(n / 2) rows of
+    // scratch; the grid is sized so that the scratch allocated for the one-sided kernel (N/2 + 1
+    // rows per thread of scratch_threads) holds every thread's rows
+    const long nwb = (cm.nitems + 31) / 32;
+    const long rows_full = N / 2 + 1, n0 = (N - 2 + 1) / 2, rows_split = (n0 + 1) / 2 + 1;
+    long cap = scratch_threads * rows_full / rows_split;
+    cap = std::max(128L, (cap / 128) * 128);
+    const long thr = std::min(cap, nwb * 128);
+    const unsigned grid2 = (unsigned)std::max(1L, thr / 128);
+    const size_t smem = sizeof(double) * (2 * ts + 2 * 32 * (6 * NC + 2));
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_solve_dirichlet2<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return e;
+    k_solve_dirichlet2<T, NC><<<grid2, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+  } else if (basis == kDirichlet) {
     const size_t smem = sizeof(double) * 2 * ts;
     if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     k_solve_dirichlet<T, NC><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
