@@ -10,9 +10,10 @@
 //        convolution of a power-of-two length instead of an O(N p) generic-radix pass),
 //        Dirichlet stencil S_k = t_k - t_{k+2}; S_k is written in FP64 into a
 //        warp-interleaved layout [warp][row][lane] (problems sorted by N, 32 per warp).
-//   K_B  one thread per (problem, parity): the FP64 elimination of k_solve.cu's Dirichlet
-//        kernel with kappa = 0, lanes = 32 problems of similar size, so every FP64 instruction
-//        serves 32 problems and every load/store of a row is one 256-byte access.
+//   K_B  two threads per (problem, parity), one per half of the rows: the two-sided FP64
+//        elimination of k_solve.cu's Dirichlet kernels with kappa = 0, lanes = 32 problems of
+//        similar size, so every FP64 instruction serves 32 problems and every load/store of a
+//        row is one 256-byte access.
 //   K_C  one CTA per problem: stencil a_k = u_k - u_{k-2} and DCT-III back to the points.
 #include <algorithm>
 
@@ -77,78 +78,140 @@ __device__ __forceinline__ double rcp64b(double x) {
   return fma(r, fma(e, e, e), r);
 }
 
-// thread = (slot, parity); U (interleaved) receives the Shen coefficients.
-// coef[k] = (-2 pi (k+1)(k+2), -4 pi (k+1)) (the diagonal and the constant upper entries of the
-// Dirichlet stiffness rows) and mass[k] = B_kk (3 pi / 2 for k = 0, else pi) come from host
-// tables: the row coefficients cost loads instead of six FP64 instructions on the critical path.
-__global__ void __launch_bounds__(128) k_batch_solve(const BatchProblem* __restrict__ probs, const int* __restrict__ by_slot,
-                                                     const long* __restrict__ wbase, const double* __restrict__ S,
-                                                     double* __restrict__ U, double* __restrict__ scratch,
-                                                     const long* __restrict__ sbase, int nslots,
-                                                     const double2* __restrict__ coef, const double* __restrict__ mass) {
-  const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;   // global warp
-  const int lane = threadIdx.x & 31;
-  const int wslot = w >> 1;          // slot warp
-  const int p = w & 1;               // parity
+// K_B.  U (interleaved) receives the Shen coefficients.  coef[k] = (-2 pi (k+1)(k+2),
+// -4 pi (k+1)) (the diagonal and the constant upper entries of the Dirichlet stiffness rows) and
+// mass[k] = B_kk (3 pi / 2 for k = 0, else pi) come from host tables: the row coefficients cost
+// loads instead of FP64 instructions on the critical path.
+// A CTA of four warps owns one slot warp (32 problems); warp (p, side) takes parity p, side 0
+// rows 0 .. h-1 top-down (mu = ell / d'_{i-1}, d'_i = d_i - mu (g'_{i-1} + ell), g'_i = g_i -
+// mu g'_{i-1}, f'_i = f_i - mu f'_{i-1}), side 1 rows
+// n-1 .. h bottom-up with u_i = a_i + b_i u_{i-1}, T_i = A_i + B_i u_{i-1} (the recurrences of
+// k_solve_dirichlet2 in k_solve.cu), h = ceil(n / 2) per problem; the halves meet through
+// shared memory at row h-1.  Rows keep their own scratch slot, so both sides share the
+// parity's scratch region.  The serial chain of the largest problems is halved.
+__global__ void __launch_bounds__(128) k_batch_solve2(const BatchProblem* __restrict__ probs, const int* __restrict__ by_slot,
+                                                      const long* __restrict__ wbase, const double* __restrict__ S,
+                                                      double* __restrict__ U, double* __restrict__ scratch,
+                                                      const long* __restrict__ sbase, int nslots,
+                                                      const double2* __restrict__ coef, const double* __restrict__ mass) {
+  __shared__ double xch[2][32][5];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p = warp & 1, side = warp >> 1;
+  const int wslot = blockIdx.x;
   const int slot = wslot * 32 + lane;
-  if (slot >= nslots) return;
-  const BatchProblem pr = probs[by_slot[slot]];
+  const bool valid = slot < nslots;
+  const BatchProblem pr = probs[by_slot[valid ? slot : wslot * 32]];
   const int N = pr.N, nb = N - 2;
   const double pi = 3.141592653589793;
   const double aB = -pr.alpha;       // a = 1, b = -alpha, kappa = 0
   const double ell = -aB * 0.5 * pi;
-  const int n = (nb - p + 1) / 2;
+  const int n = valid ? (nb - p + 1) / 2 : 0, h = (n + 1) / 2;
   const long rbase = wbase[wslot] + lane;
-  double* s = scratch + sbase[wslot] * 2 + (long)p * (sbase[wslot + 1] - sbase[wslot]) + lane;
-  double pr_ = 0.0, pg = 0.0, pge = 0.0, pf = 0.0;
-  double fn = n > 0 ? S[rbase + (long)p * 32] : 0.0;
-  double2 cn = n > 0 ? __ldg(&coef[p]) : make_double2(0.0, 0.0);
-  double mn = n > 0 ? __ldg(&mass[p]) : 0.0;
-  for (int i = 0; i < n; ++i) {
-    const int k = p + 2 * i;
-    double f = fn;
-    const double2 c = cn;
-    const double mk2 = mn;
-    if (i + 1 < n) {
-      fn = S[rbase + (long)(k + 2) * 32];
-      cn = __ldg(&coef[k + 2]);
-      mn = __ldg(&mass[k + 2]);
+  double* s0 = scratch + sbase[wslot] * 2 + (long)p * (sbase[wslot + 1] - sbase[wslot]) + lane;   // slot of row 0
+  double* x = xch[p][lane];
+  double dl = 1.0, gl = 0.0, fl = 0.0;
+  if (side == 0) {
+    double pr_ = 0.0, pg = 0.0, pge = 0.0, pf = 0.0;
+    double fn = h > 0 ? S[rbase + (long)p * 32] : 0.0;
+    double2 cn = h > 0 ? __ldg(&coef[p]) : make_double2(0.0, 0.0);
+    double mn = h > 0 ? __ldg(&mass[p]) : 0.0;
+    double* s = s0;
+    for (int i = 0; i < h; ++i) {
+      const int k = p + 2 * i;
+      double f = fn;
+      const double2 c = cn;
+      const double mk2 = mn;
+      if (i + 1 < h) {
+        fn = S[rbase + (long)(k + 2) * 32];
+        cn = __ldg(&coef[k + 2]);
+        mn = __ldg(&mass[k + 2]);
+      }
+      double d = fma(aB, mk2, c.x);
+      double g = c.y;
+      if (i > 0) {
+        const double mu = ell * pr_;
+        d = fma(-mu, pge, d);
+        g = fma(-mu, pg, g);
+        f = fma(-mu, pf, f);
+      }
+      const double r = rcp64b(d);
+      s[0] = r;
+      s[32] = g;
+      s[64] = f;
+      s += 96;
+      pr_ = r; pg = g; pge = g + ell; pf = f;
+      dl = d; gl = g; fl = f;
     }
-    double d = fma(aB, mk2, c.x);
-    double g = c.y;
-    if (i > 0) {
-      const double mu = ell * pr_;
-      d = fma(-mu, pge, d);
-      g = fma(-mu, pg, g);
-      f = fma(-mu, pf, f);
+  } else {
+    double bn = 0.0, Bn = 0.0, an = 0.0, An = 0.0;
+    double fn = n > h ? S[rbase + (long)(p + 2 * (n - 1)) * 32] : 0.0;
+    double2 cn = n > h ? __ldg(&coef[p + 2 * (n - 1)]) : make_double2(0.0, 0.0);
+    double mn = n > h ? __ldg(&mass[p + 2 * (n - 1)]) : 0.0;
+    for (int i = n - 1; i >= h; --i) {
+      const int k = p + 2 * i;
+      const double f = fn;
+      const double2 c = cn;
+      const double mk2 = mn;
+      if (i - 1 >= h) {
+        fn = S[rbase + (long)(k - 2) * 32];
+        cn = __ldg(&coef[k - 2]);
+        mn = __ldg(&mass[k - 2]);
+      }
+      const double d = fma(aB, mk2, c.x), g = c.y;
+      const double R = rcp64b(fma(g, Bn, fma(ell, bn, d)));
+      const double bi = -ell * R, onep = 1.0 + Bn;
+      const double ai = fma(-g, An, fma(-ell, an, f)) * R;
+      double* s = s0 + (long)i * 96;
+      s[0] = bi;
+      s[32] = ai;
+      An = fma(onep, ai, An);
+      Bn = onep * bi;
+      an = ai;
+      bn = bi;
     }
-    const double r = rcp64b(d);
-    s[0] = r;
-    s[32] = g;
-    s[64] = f;
-    s += 96;
-    pr_ = r; pg = g; pge = g + ell; pf = f;
+    x[0] = an;
+    x[1] = An;
+    x[2] = bn;
+    x[3] = Bn;
   }
-  double un = 0.0, Ts = 0.0;
-  double rn = 0.0, gn = 0.0, fb = 0.0;
-  if (n > 0) {
-    rn = s[-96];
-    gn = s[-64];
-    fb = s[-32];
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    const int k = p + 2 * i;
-    s -= 96;
-    const double r = rn, g = gn, f = fb;
-    if (i > 0) {   // prefetch the row above
-      rn = s[-96];
-      gn = s[-64];
-      fb = s[-32];
+  __syncthreads();
+  if (side == 0 && h > 0) {
+    const double ah = x[0], Ah = x[1], bh = x[2], Bh = x[3];
+    const double u = fma(-gl, Ah, fma(-ell, ah, fl)) * rcp64b(fma(gl, Bh, fma(ell, bh, dl)));
+    x[4] = u;
+    U[rbase + (long)(p + 2 * (h - 1)) * 32] = u;
+    double un = u, Ts = fma(Bh, u, Ah);   // T_h
+    double* s = h > 1 ? s0 + (long)(h - 2) * 96 : s0;
+    double rn = 0.0, gn = 0.0, fb = 0.0;
+    if (h > 1) {
+      rn = s[0];
+      gn = s[32];
+      fb = s[64];
     }
-    Ts += un;
-    const double u = fma(-g, Ts, fma(-ell, un, f)) * r;
-    U[rbase + (long)k * 32] = u;
-    un = u;
+    for (int i = h - 2; i >= 0; --i) {
+      const int k = p + 2 * i;
+      const double r = rn, g = gn, f = fb;
+      if (i > 0) {
+        s -= 96;
+        rn = s[0];
+        gn = s[32];
+        fb = s[64];
+      }
+      Ts += un;
+      const double uu = fma(-g, Ts, fma(-ell, un, f)) * r;
+      U[rbase + (long)k * 32] = uu;
+      un = uu;
+    }
+  }
+  __syncthreads();
+  if (side == 1 && n > h) {
+    double up = h > 0 ? x[4] : 0.0;
+    for (int i = h; i < n; ++i) {
+      const double* s = s0 + (long)i * 96;
+      const double uu = fma(s[0], up, s[32]);
+      U[rbase + (long)(p + 2 * i) * 32] = uu;
+      up = uu;
+    }
   }
 }
 
@@ -201,9 +264,8 @@ cudaError_t launch_batch(const void* f, void* u, int nprob, int nslots, int ldb,
   const BatchProblem* P = (const BatchProblem*)probs;
   k_batch_dct<T><<<nprob, 256, smem, s>>>((const T*)f, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, S,
                                           ldb);
-  const int warps = 2 * ((nslots + 31) / 32);
-  k_batch_solve<<<(warps + 3) / 4, 128, 0, s>>>(P, by_slot, wbase, S, U, scratch, sbase, nslots,
-                                                (const double2*)coef, mass);
+  k_batch_solve2<<<(nslots + 31) / 32, 128, 0, s>>>(P, by_slot, wbase, S, U, scratch, sbase, nslots,
+                                                    (const double2*)coef, mass);
   k_batch_idct<T><<<nprob, 256, smem, s>>>((T*)u, P, by_slot, (const FftPlan*)plans, (const cplx<T>*)pool, wbase, U,
                                            ldb);
   return cudaGetLastError();
