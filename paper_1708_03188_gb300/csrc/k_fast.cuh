@@ -13,15 +13,16 @@ template <typename T> __host__ __device__ constexpr int fast_elems() { return si
 template <typename T> __host__ __device__ constexpr int fast_tw_cols() { return sizeof(T) == 4 ? 16 : 8; }
 constexpr int kFastThreads = 256;
 
-// Copy TOTAL elements through registers: each thread loads up to 16 of its elements (element
-// idx = threadIdx.x + q * kFastThreads) before storing them, so the loads of a chunk are all in
-// flight at once (a generic global pointer may alias shared memory, so an interleaved
+// Copy TOTAL elements through registers: each thread loads up to 128 bytes of its elements
+// (16 complex64 or 8 pairs; element idx = threadIdx.x + q * kFastThreads) before storing them,
+// so the loads of a chunk are all in flight at once (a generic global pointer may alias shared memory, so an interleaved
 // load/store loop would wait for every load).  ld(idx) -> value, st(idx, value); both are only
 // called for idx < TOTAL.
 template <int TOTAL, typename C, typename LD, typename ST>
 __device__ __forceinline__ void staged_copy(LD ld, ST st) {
   constexpr int PER = (TOTAL + kFastThreads - 1) / kFastThreads;
-  constexpr int CH = PER < 16 ? PER : 16;
+  constexpr int CMAX = 128 / (int)sizeof(C) > 0 ? 128 / (int)sizeof(C) : 1;
+  constexpr int CH = PER < CMAX ? PER : CMAX;
 #pragma unroll 1
   for (int q0 = 0; q0 < PER; q0 += CH) {
     C v[CH];
