@@ -45,13 +45,23 @@ template <int M, int MP> __device__ __forceinline__ int gl_origidx(int q) {
 }
 template <int M> __device__ __forceinline__ int gl_wavenumber(int j) { return j < (M + 1) / 2 ? j : j - M; }
 
-template <typename T> __host__ __device__ constexpr int gl_tw() { return 4; }
+// Lines per CTA of the row passes and columns per CTA of the column pass: as many as the
+// shared-memory budget allows, reduced until the grid has at least 256 CTAs (about two per SM),
+// so that small grids do not leave SMs idle.
+template <typename T, int M, int MP> __host__ __device__ constexpr int gl_lines() {
+  int l = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  while (l > 1 && (M + l - 1) / l < 256) --l;
+  return l;
+}
+template <typename T, int MP> __host__ __device__ constexpr int gl_tw() {
+  return MP / 4 >= 256 ? 4 : (MP / 2 >= 256 ? 2 : 1);
+}
 
 template <typename T, int M, int MP>
 __global__ void __launch_bounds__(kFastThreads) k_gl_rows_pad(const cplx<T>* __restrict__ U, cplx<T>* __restrict__ P,
                                                               const cplx<T>* __restrict__ twf) {
   using C = cplx<T>;
-  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  constexpr int LINES = gl_lines<T, M, MP>();
   constexpr int LDP = pad_ld(MP);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -76,7 +86,7 @@ template <typename T, int M, int MP>
 __global__ void __launch_bounds__(kFastThreads) k_gl_cols(cplx<T>* __restrict__ P, const cplx<T>* __restrict__ twf,
                                                           double gamma) {
   using C = cplx<T>;
-  constexpr int TW = gl_tw<T>();
+  constexpr int TW = gl_tw<T, MP>();
   constexpr int LDP = pad_ld(MP);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -119,7 +129,7 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
                                                               const __grid_constant__ GlParams prm,
                                                               const cplx<T>* __restrict__ twf) {
   using C = cplx<T>;
-  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
+  constexpr int LINES = gl_lines<T, M, MP>();
   constexpr int LDP = pad_ld(MP);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
@@ -202,8 +212,8 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
 template <typename T, int M, int MP>
 cudaError_t gl_launch_sized(int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E,
                             cplx<T>* out, cplx<T>* P, const GlParams& prm, const cplx<T>* twf, cudaStream_t st) {
-  constexpr int LINES = fast_elems<T>() / MP > 0 ? fast_elems<T>() / MP : 1;
-  constexpr int TW = gl_tw<T>();
+  constexpr int LINES = gl_lines<T, M, MP>();
+  constexpr int TW = gl_tw<T, MP>();
   const size_t smem_rows = sizeof(cplx<T>) * LINES * pad_ld(MP);
   const size_t smem_cols = sizeof(cplx<T>) * TW * pad_ld(MP);
   cudaError_t e;
