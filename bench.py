@@ -488,6 +488,7 @@ def batch_measure(stream, reps=20):
         ms_serial = timed(serial)
         out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round((dof1 + dof2) / (ms * 1e-3) / 1e9, 3),
                      "graph_launches_per_batch": 1,
+                     "autotuned_plan": {"bluestein_prime": b.plan[0], "bluestein_problems": b.plan[1]},
                      "one_d_only": {"ms": round(ms1, 4), "gdof_s": round(dof1 / (ms1 * 1e-3) / 1e9, 3),
                                     "launches": 3},
                      "call_by_call_no_graph": {"ms": round(ms_serial, 4),

@@ -238,6 +238,14 @@ int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets);
  */
 int sgm_batch_helmholtz(sgm_batch* batch, const void* f, void* u, void* stream);
 /*
+ * Plan chosen at creation.  A size N whose largest prime factor exceeds *bluestein_prime runs its
+ * DFT as a Bluestein convolution of a power-of-two length; the others run their mixed-radix plan.
+ * The threshold is autotuned: sgm_batch_create times the whole batch on zero input for each of
+ * 16, 32, 64 and "never" (*bluestein_prime = 0) and keeps the fastest.  *n_bluestein counts the
+ * problems on the Bluestein path.
+ */
+int sgm_batch_info(const sgm_batch* batch, int* bluestein_prime, int* n_bluestein);
+/*
  * Add nprob independent 2-D problems  a lap(u_q) + b u_q = f_q  on [-1, 1] x [0, 2 pi), each
  * on its own Shen-Dirichlet x R2C Fourier space (the 2-D Poisson problem of Sec. 4, solved as
  * sgm_helmholtz does: scalar product, per-wavenumber FP64 elimination, backward transform).

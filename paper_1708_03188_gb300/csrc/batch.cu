@@ -45,6 +45,7 @@ struct sgm_batch {
   int nprob = 0, Nmax = 0;
   int ldb = 0;                    // shared-memory buffer length of the transform kernels
   int nbluestein = 0;             // problems whose DFT runs as a Bluestein convolution
+  int bluestein_prime = 0;        // the autotuned threshold on the largest prime factor
   long total = 0;                 // sum of N
   std::vector<int64_t> offsets;   // nprob + 1
   void* probs = nullptr;
@@ -122,8 +123,9 @@ int largest_prime_factor(int n) {
   return n > 1 ? std::max(best, n) : best;
 }
 
-// sizes with a prime factor above this run their DFT as a Bluestein convolution
-constexpr int kBluesteinPrime = 32;
+// candidate thresholds of the batch autotuner: a size whose largest prime factor is above the
+// threshold runs its DFT as a Bluestein convolution; kNoBluestein disables it
+constexpr int kNoBluestein = 1 << 30;
 
 // in-place radix-2 DFT of a power-of-two length (exp(-2 pi i j k / L)), long double
 void host_fft(std::vector<long double>& re, std::vector<long double>& im) {
@@ -180,26 +182,30 @@ template <typename T> void push_bluestein(std::vector<cplx<T>>& pool, int N, int
   for (int m = 0; m < L; ++m) pool.push_back(mk<cplx<T>>((T)(br[m] / L), (T)(bi[m] / L)));
 }
 
-template <typename T> int build(sgm_batch* b, const int64_t* n, const double* alpha) {
+// Size-dependent tables for one Bluestein threshold: a size N whose largest prime factor exceeds
+// `prime` runs its DFT as a Bluestein convolution, every other size through its own mixed-radix
+// plan.  Fills the plan fields of probs (not the slots) and returns the shared-memory buffer
+// length of the transform kernels.  `blue` caches the chirp tables per size across thresholds.
+template <typename T>
+int plan_tables(const sgm_batch* b, const int64_t* n, const double* alpha, int prime,
+                std::map<int, std::vector<cplx<T>>>& blue, std::vector<BatchProblemH>& probs,
+                std::vector<FftPlan>& plans, std::vector<cplx<T>>& pool, int& nblue) {
   const int P = b->nprob;
-  std::vector<int> order(P);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return n[x] > n[y]; });
   std::map<int, int> size_index;   // N -> plan index
-  std::vector<FftPlan> plans;
-  std::vector<cplx<T>> pool;
   std::vector<int> tw_off, dct_off, conv_len, chirp_off, bhat_off;
-  std::vector<BatchProblemH> probs(P);
-  b->ldb = b->Nmax + 1;
+  plans.clear();
+  pool.clear();
+  nblue = 0;
+  int ldb = b->Nmax + 1;
   for (int p = 0; p < P; ++p) {
     const int N = (int)n[p];
     if (!size_index.count(N)) {
       size_index[N] = (int)plans.size();
       int L = 0, co = 0, bo = 0;
-      if (largest_prime_factor(N) > kBluesteinPrime) {
+      if (largest_prime_factor(N) > prime) {
         L = 1;
         while (L < 2 * N - 1) L *= 2;
-        b->ldb = std::max(b->ldb, L);
+        ldb = std::max(ldb, L);
       }
       const int Lf = L ? L : N;
       plans.push_back(host_plan(Lf));
@@ -207,15 +213,36 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
       push_twiddles<T>(pool, Lf, (long double)Lf / 2.0L);  // exp(-2 pi i k / Lf)
       dct_off.push_back((int)pool.size());
       push_twiddles<T>(pool, N, 2.0L * N);                 // exp(-i pi k / (2N))
-      if (L) push_bluestein<T>(pool, N, L, co, bo);
+      if (L) {
+        auto it = blue.find(N);
+        if (it == blue.end()) {
+          std::vector<cplx<T>> tab;
+          int c0 = 0, b0 = 0;
+          push_bluestein<T>(tab, N, L, c0, b0);   // chirp (N values) then bhat (L values)
+          it = blue.emplace(N, std::move(tab)).first;
+        }
+        co = (int)pool.size();
+        bo = co + N;
+        pool.insert(pool.end(), it->second.begin(), it->second.end());
+      }
       conv_len.push_back(L);
       chirp_off.push_back(co);
       bhat_off.push_back(bo);
     }
     const int pi = size_index[N];
-    probs[p] = {N, 0, (long)b->offsets[p], alpha[p], tw_off[pi], dct_off[pi], pi, conv_len[pi], chirp_off[pi], bhat_off[pi]};
-    if (conv_len[pi]) ++b->nbluestein;
+    const int slot = probs[p].slot;
+    probs[p] = {N, slot, (long)b->offsets[p], alpha[p], tw_off[pi], dct_off[pi], pi, conv_len[pi], chirp_off[pi], bhat_off[pi]};
+    if (conv_len[pi]) ++nblue;
   }
+  return ldb;
+}
+
+template <typename T> int build(sgm_batch* b, const int64_t* n, const double* alpha) {
+  const int P = b->nprob;
+  std::vector<int> order(P);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return n[x] > n[y]; });
+  std::vector<BatchProblemH> probs(P);
   std::vector<int> by_slot(P);
   for (int s = 0; s < P; ++s) {
     by_slot[s] = order[s];
@@ -237,10 +264,7 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
     e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
     if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
   };
-  up(&b->probs, probs.data(), sizeof(BatchProblemH) * P);
   up((void**)&b->by_slot, by_slot.data(), sizeof(int) * P);
-  up(&b->plans, plans.data(), sizeof(FftPlan) * plans.size());
-  up(&b->pool, pool.data(), sizeof(cplx<T>) * pool.size());
   up((void**)&b->wbase, wbase.data(), sizeof(long) * wbase.size());
   up((void**)&b->sbase, sbase.data(), sizeof(long) * sbase.size());
   {
@@ -258,7 +282,73 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   if (e == cudaSuccess) e = cudaMalloc(&b->U, sizeof(double) * wbase[nw]);
   if (e == cudaSuccess) e = cudaMalloc(&b->scratch, sizeof(double) * 2 * sbase[nw]);
   if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch set-up: %s", cudaGetErrorString(e));
-  return SGM_OK;
+
+  // size-dependent tables; with problems present, the Bluestein threshold is autotuned: the whole
+  // batch (three kernels) is timed on zero input for each candidate and the fastest is kept
+  std::map<int, std::vector<cplx<T>>> blue;
+  std::vector<FftPlan> plans;
+  std::vector<cplx<T>> pool;
+  auto install = [&](int prime) -> int {
+    cudaFree(b->probs);
+    cudaFree(b->plans);
+    cudaFree(b->pool);
+    b->probs = b->plans = b->pool = nullptr;
+    int nblue = 0;
+    b->ldb = plan_tables<T>(b, n, alpha, prime, blue, probs, plans, pool, nblue);
+    b->nbluestein = nblue;
+    b->bluestein_prime = prime;
+    up(&b->probs, probs.data(), sizeof(BatchProblemH) * P);
+    up(&b->plans, plans.data(), sizeof(FftPlan) * plans.size());
+    up(&b->pool, pool.data(), sizeof(cplx<T>) * pool.size());
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch tables: %s", cudaGetErrorString(e));
+    return SGM_OK;
+  };
+  const int candidates[] = {16, 32, 64, kNoBluestein};
+  int best = 32;
+  if (P > 0) {
+    void* f = nullptr;
+    void* u = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t te = cudaMalloc(&f, sizeof(T) * (size_t)b->total);
+    if (te == cudaSuccess) te = cudaMalloc(&u, sizeof(T) * (size_t)b->total);
+    if (te == cudaSuccess) te = cudaMemset(f, 0, sizeof(T) * (size_t)b->total);
+    if (te == cudaSuccess) te = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (te == cudaSuccess) te = cudaEventCreate(&e0);
+    if (te == cudaSuccess) te = cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    for (int prime : candidates) {
+      if (te != cudaSuccess) break;
+      const int st_ = install(prime);
+      if (st_ != SGM_OK) {
+        te = cudaErrorUnknown;
+        break;
+      }
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4 && te == cudaSuccess; ++rep) {
+        te = cudaEventRecord(e0, st);
+        if (te == cudaSuccess)
+          te = launch_batch<T>(f, u, b->nprob, b->nprob, b->ldb, b->probs, b->by_slot, b->plans, b->pool, b->wbase,
+                               b->S, b->U, b->scratch, b->sbase, b->coef, b->mass, st);
+        if (te == cudaSuccess) te = cudaEventRecord(e1, st);
+        if (te == cudaSuccess) te = cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        if (te == cudaSuccess) te = cudaEventElapsedTime(&ms, e0, e1);
+        if (te == cudaSuccess && rep > 0) ms_min = std::min(ms_min, ms);   // the first run sets attributes
+      }
+      if (te == cudaSuccess && ms_min < best_ms) {
+        best_ms = ms_min;
+        best = prime;
+      }
+    }
+    cudaFree(f);
+    cudaFree(u);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (te != cudaSuccess) return set_error(SGM_ERR_CUDA, "batch autotune: %s", cudaGetErrorString(te));
+  }
+  return install(best);
 }
 
 constexpr int kBranches = 64;
@@ -470,6 +560,14 @@ int sgm_batch_add_2d(sgm_batch* b, int nprob, const int64_t* sizes, double a, do
     b->p2[q].branch = 1 + i;
     load[i] += cost[q];
   }
+  return SGM_OK;
+}
+
+int sgm_batch_info(const sgm_batch* b, int* bluestein_prime, int* n_bluestein) {
+  if (!b || !bluestein_prime || !n_bluestein) return set_error(SGM_ERR_NULL, "NULL argument");
+  if (b->magic != sgm_batch::kMagic) return set_error(SGM_ERR_STATE, "not a live sgm_batch");
+  *bluestein_prime = b->bluestein_prime >= kNoBluestein ? 0 : b->bluestein_prime;
+  *n_bluestein = b->nbluestein;
   return SGM_OK;
 }
 

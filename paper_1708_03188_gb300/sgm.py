@@ -44,6 +44,7 @@ _SIGNATURES = {
     "sgm_batch_destroy": (ctypes.c_int, [_VP]),
     "sgm_batch_offsets": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "sgm_batch_helmholtz": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "sgm_batch_info": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
     "sgm_batch_add_2d": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64), _D, _D]),
     "sgm_batch_offsets_2d": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int64)]),
     "sgm_batch_run": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
@@ -265,6 +266,13 @@ class Batch:
         self.dtype = torch.float32 if precision == "f32" else torch.float64
         self.sizes2d = []
         self.offsets2d = [0]
+
+    @property
+    def plan(self):
+        """(Bluestein prime threshold chosen by the autotuner, 0 for never; problems on that path)."""
+        p, nb = ctypes.c_int(), ctypes.c_int()
+        check(lib().sgm_batch_info(self._h, ctypes.byref(p), ctypes.byref(nb)))
+        return p.value, nb.value
 
     def add_2d(self, sizes2d, a=-1.0, b=0.0):
         """Add 2-D problems of sizes [(N, M), ...] solving a lap(u) + b u = f."""

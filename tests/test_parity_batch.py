@@ -235,3 +235,22 @@ def test_batch_2d_errors():
         bt.add_2d([(16, 16)])                       # only once
     with pytest.raises(ValueError):
         bt.run(torch.zeros(16, device="cuda"), None)
+
+
+@pytest.mark.gpu
+def test_autotuned_plan_is_reported():
+    from paper_1708_03188_gb300.sgm import Batch
+    sizes, alpha, _ = inputs.batch1d(512)
+    bt = Batch(sizes, alpha, "f32")
+    prime, nblue = bt.plan
+    assert prime in (0, 16, 32, 64)
+
+    def lpf(n):
+        best, m, q = 1, int(n), 2
+        while q * q <= m:
+            while m % q == 0:
+                best, m = q, m // q
+            q += 1
+        return max(best, m) if m > 1 else best
+    expect = 0 if prime == 0 else sum(1 for n in sizes if lpf(n) > prime)
+    assert nblue == expect
