@@ -477,6 +477,12 @@ def batch_measure(stream, reps=20):
         u2 = torch.empty_like(f2)
         ms = timed(lambda: b.run(f1, f2, out1=u1, out2=u2, stream=stream))
         ms1 = timed(lambda: b.solve(f1, out=u1, stream=stream))
+        bd = Batch(sizes, alpha, prec, autotune=False)      # the default plan, for comparison
+        bd.add_2d(sizes2d, -1.0, 0.0)
+        u1d, u2d = torch.empty_like(f1), torch.empty_like(f2)
+        ms_default = timed(lambda: bd.run(f1, f2, out1=u1d, out2=u2d, stream=stream))
+        ms1_default = timed(lambda: bd.solve(f1, out=u1d, stream=stream))
+        bd.close()
         spaces = [Space(["dirichlet", "r2c"], (N, M), precision=prec) for N, M in sizes2d]
         views = [(f2[b.offsets2d[q]:b.offsets2d[q] + N * M].view(N, M), u2[b.offsets2d[q]:b.offsets2d[q] + N * M].view(N, M))
                  for q, (N, M) in enumerate(sizes2d)]
@@ -489,6 +495,8 @@ def batch_measure(stream, reps=20):
         out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round((dof1 + dof2) / (ms * 1e-3) / 1e9, 3),
                      "graph_launches_per_batch": 1,
                      "autotuned_plan": {"bluestein_prime": b.plan[0], "bluestein_problems": b.plan[1]},
+                     "default_plan": {"bluestein_prime": 32, "ms_per_batch": round(ms_default, 4),
+                                      "one_d_only_ms": round(ms1_default, 4)},
                      "one_d_only": {"ms": round(ms1, 4), "gdof_s": round(dof1 / (ms1 * 1e-3) / 1e9, 3),
                                     "launches": 3},
                      "call_by_call_no_graph": {"ms": round(ms_serial, 4),

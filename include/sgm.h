@@ -227,6 +227,9 @@ typedef struct sgm_batch sgm_batch;
  * are then ignored) for a batch of 2-D problems only (sgm_batch_add_2d).
  */
 int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double* alpha, int precision);
+/* or-ed into the precision of sgm_batch_create: keep the default plan (Bluestein above a largest
+ * prime factor of 32) instead of autotuning it (see sgm_batch_info) */
+#define SGM_BATCH_FIXED_PLAN 0x40
 int sgm_batch_destroy(sgm_batch* batch);
 /* Element offsets of the problems in the packed arrays: offsets[p] = n[0] + ... + n[p-1], nprob+1 entries. */
 int sgm_batch_offsets(const sgm_batch* batch, int64_t* offsets);

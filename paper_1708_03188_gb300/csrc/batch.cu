@@ -237,7 +237,7 @@ int plan_tables(const sgm_batch* b, const int64_t* n, const double* alpha, int p
   return ldb;
 }
 
-template <typename T> int build(sgm_batch* b, const int64_t* n, const double* alpha) {
+template <typename T> int build(sgm_batch* b, const int64_t* n, const double* alpha, bool autotune) {
   const int P = b->nprob;
   std::vector<int> order(P);
   std::iota(order.begin(), order.end(), 0);
@@ -305,7 +305,7 @@ template <typename T> int build(sgm_batch* b, const int64_t* n, const double* al
   };
   const int candidates[] = {16, 32, 64, kNoBluestein};
   int best = 32;
-  if (P > 0) {
+  if (P > 0 && autotune) {
     void* f = nullptr;
     void* u = nullptr;
     cudaStream_t st = nullptr;
@@ -467,6 +467,8 @@ int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double*
   *out = nullptr;
   if (nprob < 0) return set_error(SGM_ERR_SIZE, "nprob must be >= 0");
   if (nprob > 0 && (!n || !alpha)) return set_error(SGM_ERR_NULL, "n and alpha must be non-NULL");
+  const bool fixed_plan = (precision & SGM_BATCH_FIXED_PLAN) != 0;
+  precision &= ~SGM_BATCH_FIXED_PLAN;
   if (precision != SGM_F32 && precision != SGM_F64) return set_error(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
   for (int p = 0; p < nprob; ++p) {
     if (n[p] < 4 || n[p] > 4096) return set_error(SGM_ERR_SIZE, "problem %d: N = %lld outside 4..4096", p, (long long)n[p]);
@@ -487,7 +489,7 @@ int sgm_batch_create(sgm_batch** out, int nprob, const int64_t* n, const double*
     b->Nmax = std::max(b->Nmax, (int)n[p]);
   }
   b->total = (long)b->offsets[nprob];
-  const int st = precision == SGM_F32 ? build<float>(b, n, alpha) : build<double>(b, n, alpha);
+  const int st = precision == SGM_F32 ? build<float>(b, n, alpha, !fixed_plan) : build<double>(b, n, alpha, !fixed_plan);
   if (st != SGM_OK) {
     free_batch(b);
     return st;

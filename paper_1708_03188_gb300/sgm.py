@@ -252,14 +252,15 @@ class Batch:
     and optionally 2-D problems a lap(u_q) + b u_q = f_q on Shen-Dirichlet x R2C spaces (packed
     row-major N x M arrays at offsets2d[q])."""
 
-    def __init__(self, sizes, alpha, precision="f32"):
+    def __init__(self, sizes, alpha, precision="f32", autotune=True):
         self.sizes = [int(v) for v in sizes]
         self.precision = precision
         nprob = len(self.sizes)
         n = (ctypes.c_int64 * max(nprob, 1))(*self.sizes)
         a = (_D * max(nprob, 1))(*[float(v) for v in alpha])
         self._h = _VP()
-        check(lib().sgm_batch_create(ctypes.byref(self._h), nprob, n, a, PRECISION[precision]))
+        check(lib().sgm_batch_create(ctypes.byref(self._h), nprob, n, a,
+                                     PRECISION[precision] | (0 if autotune else 0x40)))
         off = (ctypes.c_int64 * (nprob + 1))()
         check(lib().sgm_batch_offsets(self._h, off))
         self.offsets = [int(v) for v in off]

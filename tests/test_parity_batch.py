@@ -254,3 +254,5 @@ def test_autotuned_plan_is_reported():
         return max(best, m) if m > 1 else best
     expect = 0 if prime == 0 else sum(1 for n in sizes if lpf(n) > prime)
     assert nblue == expect
+    fixed = Batch(sizes, alpha, "f32", autotune=False)
+    assert fixed.plan == (32, sum(1 for n in sizes if lpf(n) > 32))
