@@ -32,7 +32,9 @@
 // l1 = -M1/2 have no partner and are solved as a pair of identical columns.  When both
 // Fourier axes have the same length and domain, (l1, l2) and (l2, l1) share kappa2 too and
 // one thread eliminates the four columns (+-a, b), (+-b, a) (NC = 4): fewer FP64 operations
-// per column and about one warp per SM sub-partition on the 256^3 box.  Warps own 32
+// per column and about one warp per SM sub-partition on the 256^3 box (the space uses it for the
+// biharmonic elimination, whose factorisation dominates; the Dirichlet one keeps pairs and twice
+// the warps).  1-D and 2-D spaces use the two-sided kernel k_solve_dirichlet2.  Warps own 32
 // consecutive work items of one parity, so every load and store of a row is coalesced.
 // The per-row reduced quantities go to a global FP64 scratch laid out [row][value][thread]
 // (a warp touches 256 contiguous bytes) and are read back by the back substitution.
