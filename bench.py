@@ -163,7 +163,7 @@ def hbm_peak():
 # square box) plus the per-column right-hand-side work (16 and 34)
 FLOPS_PER_ROW = {"dirichlet": 15 / 2 + 16, "biharmonic": 53 / 4 + 34}
 # DRAM bytes (read + write) of one k_solve_biharmonic<double, 4> launch on the 256^3 box, from
-# ncu (dram__bytes_read.sum + dram__bytes_write.sum; profiles/k_solve_biharmonic_box3d_256.md)
+# one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum)
 BIH_TRAFFIC_BYTES = 309_025_280 + 318_420_736
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
 
