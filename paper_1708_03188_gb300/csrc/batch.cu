@@ -126,6 +126,8 @@ int largest_prime_factor(int n) {
 // candidate thresholds of the batch autotuner: a size whose largest prime factor is above the
 // threshold runs its DFT as a Bluestein convolution; kNoBluestein disables it
 constexpr int kNoBluestein = 1 << 30;
+// shared memory one transform CTA may use (the opt-in maximum of a CTA on sm_103a is 227 KB)
+constexpr size_t kMaxBatchSmem = 227 * 1024;
 
 // in-place radix-2 DFT of a power-of-two length (exp(-2 pi i j k / L)), long double
 void host_fft(std::vector<long double>& re, std::vector<long double>& im) {
@@ -205,7 +207,10 @@ int plan_tables(const sgm_batch* b, const int64_t* n, const double* alpha, int p
       if (largest_prime_factor(N) > prime) {
         L = 1;
         while (L < 2 * N - 1) L *= 2;
-        ldb = std::max(ldb, L);
+        // the two convolution buffers must fit a CTA's shared memory (227 KB); larger sizes
+        // (FP64 beyond N = 2048) keep their direct plan
+        if (2 * sizeof(cplx<T>) * (size_t)L > kMaxBatchSmem) L = 0;
+        else ldb = std::max(ldb, L);
       }
       const int Lf = L ? L : N;
       plans.push_back(host_plan(Lf));

@@ -256,3 +256,26 @@ def test_autotuned_plan_is_reported():
     assert nblue == expect
     fixed = Batch(sizes, alpha, "f32", autotune=False)
     assert fixed.plan == (32, sum(1 for n in sizes if lpf(n) > 32))
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 5e-5)])
+def test_sizes_up_to_the_limit_manufactured(prec, tol):
+    # N up to the 4096 limit, prime sizes among them: the FP64 Bluestein buffers of N > 2048 would
+    # not fit a CTA's shared memory, so those sizes keep their direct plan
+    def exact(x):
+        return (1 - x * x) * np.exp(x) * np.sin(3 * x)
+
+    def second(x):
+        e, s3, c3 = np.exp(x), np.sin(3 * x), np.cos(3 * x)
+        g, g1, g2 = 1 - x * x, -2 * x, -2.0
+        h, h1, h2 = e * s3, e * (s3 + 3 * c3), e * (-8 * s3 + 6 * c3)
+        return g2 * h + 2 * g1 * h1 + g * h2
+
+    sizes = [4096, 4093, 3001, 4078, 17]
+    alpha = [10.0, 0.0, 1e4, 250.0, 3.0]
+    fs = [second(inputs.cheb_points(N)) - a * exact(inputs.cheb_points(N)) for N, a in zip(sizes, alpha)]
+    b, u, _ = run(sizes, alpha, fs, prec)
+    for p, N in enumerate(sizes):
+        ue = exact(inputs.cheb_points(N))
+        err = np.linalg.norm(u[b.offsets[p]:b.offsets[p + 1]] - ue) / np.linalg.norm(ue)
+        assert err < tol, (N, err)
