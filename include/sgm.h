@@ -93,8 +93,8 @@ const char* sgm_status_string(int status);
  *   out        receives the new space.
  *   ndim       1..3.
  *   kinds      ndim basis kinds (see above).
- *   n          ndim sizes: quadrature points per axis (N >= 4 for Dirichlet, N >= 6 for
- *              biharmonic; Fourier sizes >= 1).  Every size <= 4096.
+ *   n          ndim sizes: quadrature points per axis (N >= 4 for Dirichlet, 6 <= N <= 2048
+ *              for biharmonic; Fourier sizes >= 1).  Every size <= 4096.
  *   domain     2*ndim doubles (lo, hi) per axis, or NULL for [-1,1] on a Chebyshev axis
  *              and [0, 2 pi) on a Fourier axis.  A Fourier axis of length L = hi - lo is
  *              mapped onto [0, 2 pi), so its derivatives scale by 2 pi / L (Sec. 6).

@@ -544,6 +544,9 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   }
   if (kinds[0] == SGM_SHEN_DIRICHLET && n[0] < 4) return fail(SGM_ERR_SIZE, "Dirichlet basis needs N >= 4");
   if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "biharmonic basis needs N >= 6");
+  // the biharmonic elimination stages 13 coefficient tables of N + 8 doubles in shared memory
+  if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] > 2048)
+    return fail(SGM_ERR_SIZE, "biharmonic basis needs N <= 2048 (got %lld)", (long long)n[0]);
   if (kinds[0] == SGM_CHEBYSHEV && n[0] < 2) return fail(SGM_ERR_SIZE, "Chebyshev basis needs N >= 2");
   if (kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] < 2) return fail(SGM_ERR_SIZE, "R2C axis needs M >= 2");
   if ((cheb_flags & SGM_CHEB_TC) && (!cheb || n[0] > kTcMaxN))

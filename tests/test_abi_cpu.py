@@ -51,6 +51,7 @@ def test_status_strings(libsgm):
     (2, [4, 3], [8, 8], -2),           # R2C not on the last axis
     (1, [1], [3], -2),                 # Dirichlet needs N >= 4
     (1, [2], [5], -2),                 # biharmonic needs N >= 6
+    (1, [2], [2049], -2),              # biharmonic needs N <= 2048 (shared-memory tables)
     (1, [9], [8], -3),                 # unknown kind
     (1, [3], [5000], -2),              # size limit
 ])
