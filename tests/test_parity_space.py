@@ -237,3 +237,31 @@ def test_errors_are_raised():
         gb.helmholtz_solve(1.0, 0.0, gb.empty_spectral())   # wrong basis
     with pytest.raises(SgmError):
         gs.helmholtz(-1.0, 0.0, x, out=x)           # aliasing physical in/out
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32", 5e-5)])
+@pytest.mark.parametrize("N", [4096, 4093])
+def test_dirichlet_at_the_size_limit_manufactured(prec, tol, N):
+    # the largest Chebyshev axis (4096) and a large prime one (4093, generic-radix DFT), 1-D and
+    # 2-D: u = (1 - x^2) exp(x) sin(3x) (times cos 2y in 2-D) against a u'' - alpha u = f with
+    # f in closed form
+    def exact(x):
+        return (1 - x * x) * np.exp(x) * np.sin(3 * x)
+
+    def second(x):
+        e, s3, c3 = np.exp(x), np.sin(3 * x), np.cos(3 * x)
+        g, g1, g2 = 1 - x * x, -2 * x, -2.0
+        h, h1, h2 = e * s3, e * (s3 + 3 * c3), e * (-8 * s3 + 6 * c3)
+        return g2 * h + 2 * g1 * h1 + g * h2
+
+    alpha = 40.0
+    x = inputs.cheb_points(N)
+    gs = gspace(["dirichlet"], [N], prec)
+    u = to_np(gs.helmholtz(1.0, -alpha, to_dev(second(x) - alpha * exact(x), gs.physical_dtype)))
+    assert rel(u, exact(x)) < tol
+    # 2-D: lap u - alpha u with u = exact(x) cos 2y, so f = (u_xx - (4 + alpha) u) cos 2y
+    g2 = gspace(["dirichlet", "r2c"], [N, 8], prec)
+    xx, yy = inputs.mesh(["dirichlet", "r2c"], (N, 8))
+    f2 = (second(xx) - (4.0 + alpha) * exact(xx)) * np.cos(2 * yy)
+    u2 = to_np(g2.helmholtz(1.0, -alpha, to_dev(f2, g2.physical_dtype)))
+    assert rel(u2, exact(xx) * np.cos(2 * yy)) < tol
