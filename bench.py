@@ -233,14 +233,6 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    # The step (14 kernels on two streams) is captured once as a CUDA graph and replayed, so the
-    # timed loop does not depend on how fast the host issues launches.
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step()
-    for _ in range(2):
-        graph.replay()
-    torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
@@ -251,7 +243,7 @@ def run_ours(args):
             dist.barrier()
         e0.record(stream)
         for _ in range(args.steps):
-            graph.replay()
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
         if world > 1:
@@ -391,9 +383,7 @@ def run_ours(args):
             "config": {"workload": "box3d 256^3: Poisson (Shen-Dirichlet) + biharmonic (Shen-biharmonic) x "
                                    "Fourier C2C 256 x R2C 256, physical f -> physical u",
                        "global_batch": world, "dof_per_step": DOF_PER_STEP, "parallelism": f"replicas x{world}",
-                       "l2": "working set > L2 (two 64 MiB inputs, two 64 MiB outputs, 4 x 64.5 MiB workspaces)",
-                       "launch": "step captured once as a CUDA graph (Poisson and biharmonic solves on two "
-                                 "streams), replayed once per step"},
+                       "l2": "working set > L2 (two 64 MiB inputs, two 64 MiB outputs, 4 x 64.5 MiB workspaces)"},
             "error_vs_exact": {"poisson": err_p, "biharmonic": err_b},
             "breakdown_ms": {k: round(v, 4) for k, v in br.items()},
             "roofline": roofline,
