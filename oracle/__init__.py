@@ -11,7 +11,8 @@ Modules
   quadrature      Chebyshev-Gauss points/weights and basis values (Sec. 3.4.2).
   fourier         dense Fourier transforms and wavenumbers (Sec. 3.4.1).
   galerkin        mass / stiffness / bi-harmonic matrices by quadrature (Sec. 3.4.2, Sec. 4).
-  space           tensor-product scalar product, forward, backward and solves (Sec. 4).
+  space           tensor-product scalar product, forward, backward and solves (Sec. 4),
+                  projected derivatives (Sec. 5).
   ginzburg_landau padded nonlinear term and RK4 steppers (Sec. 6).
   closure_cnn     periodic 3x3 convolution network, forward and backward (FP64).
 

@@ -143,3 +143,44 @@ class Space:
         mats = self.matrices()
         return galerkin.solve_columns(self.kinds[0], self.sizes[0], f_tilde, self.kappa2(),
                                       lambda k2: galerkin.biharmonic_matrix(mats, a, b, c, k2))
+
+    # ---- derivatives (Sec. 5) ------------------------------------------------------------
+    def project_dx(self, u_hat, axis, order):
+        """project(Dx(u, axis, order), W0) of Sec. 5 for the Function with coefficients u_hat.
+
+        W0 is this space with axis 0 replaced by the regular Chebyshev basis (W0 is the space
+        itself when every axis is a Fourier axis).  The projection onto W0 is the forward
+        transform of Sec. 3.4.2 applied to the derivative, written with Galerkin matrices:
+          Chebyshev axis    B0^{-1} C u_hat, with C[k, l] = (d^m phi_l / dx^m, T_k)_w^N and the
+                            regular basis' mass matrix B0[k, j] = (T_j, T_k)_w^N, both by
+                            Gauss-Chebyshev quadrature (the projection of the basis functions
+                            alone, m = 0, when the derivative is along a Fourier axis);
+          Fourier axis d    the Fourier inner products of Sec. 3.4.1 give the factor
+                            (i k)^m, k = 2 pi l / L_d with the stored wavenumber l (FFT order;
+                            an R2C axis keeps l = 0..M/2).
+        Rows of u_hat past the basis size are ignored.  Returns the coefficients in W0's
+        spectral layout (all N rows along axis 0).
+        """
+        u_hat = np.asarray(u_hat)
+        ndim = len(self.kinds)
+        assert 0 <= axis < ndim and order >= 0
+        out = u_hat.astype(np.complex128 if np.iscomplexobj(u_hat) else np.float64)
+        if self.has_cheb:
+            kind, N = self.kinds[0], self.sizes[0]
+            m0 = order if axis == 0 else 0
+            x, w = quadrature.gauss_points(N)
+            T = quadrature.basis_values("chebyshev", N, x)        # T_k(x_j), (N, N)
+            V = quadrature.basis_values(kind, N, x, deriv=m0)     # phi_l^(m0)(x_j), (N, nb)
+            nb = V.shape[1]
+            Tw = T * w[:, None]
+            C = Tw.T @ V
+            B0 = Tw.T @ T
+            out = np.tensordot(np.linalg.solve(B0, C), out[:nb], axes=([1], [0]))
+        if not (self.has_cheb and axis == 0):
+            M = self.sizes[axis]
+            L = self.domains[axis][1] - self.domains[axis][0]
+            k = fourier.wavenumbers(M, r2c=self.kinds[axis] == "r2c") * (2 * np.pi / L)
+            view = [1] * ndim
+            view[axis] = -1
+            out = out * ((1j * k) ** order).reshape(view)
+        return out
