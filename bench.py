@@ -152,15 +152,12 @@ def hbm_peak():
 
 
 # FP64 operations (an FMA counts 2) per Chebyshev row per complex Fourier column in the
-# eliminations of k_solve.cu on the 256^3 box, where the four columns (+-a, b), (+-b, a) share
-# one factorisation:
-#   Dirichlet  (15 per row of the shared factorisation) / 4 + 16 per right-hand-side column = 19.75
-#   biharmonic (53 per row of the shared factorisation) / 4 + 34 per right-hand-side column = 47.25
-# (row assembly from the coefficient tables, elimination of the sub-diagonal entries, one
-# reciprocal = approximation + cubic Newton step, back substitution with the tail sums).
-# algorithmic FP64 flops per row per Fourier column of one elimination: the factorisation (15
-# Dirichlet, 53 biharmonic) shared by the columns of one thread (2 Dirichlet, 4 biharmonic on the
-# square box) plus the per-column right-hand-side work (16 and 34)
+# eliminations of k_solve.cu on the 256^3 box: the factorisation of a row (15 Dirichlet, 53
+# biharmonic: row assembly from the coefficient tables, elimination of the sub-diagonal entries,
+# one reciprocal = approximation + cubic Newton step) shared by the columns of one thread (the
+# pairs +-m for Dirichlet, the quadruples (+-a, b), (+-b, a) for the biharmonic solve on the
+# square box), plus the per-column right-hand-side work with the tail sums (16 and 34):
+#   Dirichlet  15 / 2 + 16 = 23.5,  biharmonic  53 / 4 + 34 = 47.25
 FLOPS_PER_ROW = {"dirichlet": 15 / 2 + 16, "biharmonic": 53 / 4 + 34}
 # DRAM bytes (read + write) of one k_solve_biharmonic<double, 4> launch on the 256^3 box, from
 # one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum)
@@ -369,6 +366,7 @@ def run_ours(args):
     gl = gl_measure(Space, stream, steps=args.gl_steps) if args.gl_steps > 0 else None
     batch = batch_measure(stream)
     closure_res = closure_measure(stream) if args.gl_steps > 0 else None
+    project = project_measure(sp_b, sb_rhs, stream)
 
     value = world * DOF_PER_STEP / (ms * 1e-3) / 1e9
     line = None
@@ -396,12 +394,46 @@ def run_ours(args):
             "gl": gl,
             "batch": batch,
             "closure": closure_res,
+            "project_dx": project,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
     return line
+
+
+def project_measure(sp, u_hat, stream, reps=20):
+    """project(Dx(u, axis, m), W0) on the 256^3 FP32 biharmonic x C2C x R2C box (Sec. 5: du/dx of
+    the biharmonic solution onto the regular Chebyshev space), one launch each, CUDA events.
+    Two input/output pairs alternate, 270 MB in all, so successive launches miss in L2.
+    Algorithmic bytes per launch: read 8 B + write 8 B per complex coefficient."""
+    import torch
+    try:
+        ins = [u_hat, u_hat.clone()]
+        outs = [torch.empty_like(u_hat), torch.empty_like(u_hat)]
+        nbytes = 2 * u_hat.element_size() * u_hat.numel()
+        peak, src = hbm_peak()
+        res = {"workload": f"box3d 256^3 {sp.precision} biharmonic x C2C x R2C spectral array "
+                           f"(256 x 256 x 129 {str(u_hat.dtype).replace('torch.', '')})",
+               "algorithmic_bytes_per_launch": nbytes, "peak_gbs": peak, "peak_source": src, "cases": {}}
+        for name, axis, m in (("dx", 0, 1), ("dxx", 0, 2), ("dy", 1, 1)):
+            for i in range(3):
+                sp.project_dx(ins[i % 2], axis, m, out=outs[i % 2])
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(reps):
+                sp.project_dx(ins[i % 2], axis, m, out=outs[i % 2])
+            b.record(stream)
+            b.synchronize()
+            ms = a.elapsed_time(b) / reps
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            res["cases"][name] = {"axis": axis, "order": m, "ms": round(ms, 4), "gbs": round(gbs, 1),
+                                  "frac": round(gbs / peak, 3)}
+        return res
+    except Exception as e:  # reported in the line; the step's numbers above stand
+        return {"error": f"{type(e).__name__}: {e}"}
 
 
 def gl_measure(Space, stream, M=512, steps=200):

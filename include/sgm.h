@@ -188,6 +188,28 @@ int sgm_helmholtz(sgm_space* space, double a, double b, const void* f, void* u, 
 int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f, void* u,
                    void* stream);
 
+/*
+ * Projected derivative, project(Dx(u, axis, order), W0) of Sec. 5: the coefficients in W0 of
+ * the order-th partial derivative along `axis` of the Function u whose coefficients in this
+ * space are u_hat.  W0 is this space with axis 0 replaced by SGM_CHEBYSHEV (same sizes, domain
+ * and precision); when every axis is a Fourier axis, W0 is this space itself.  The projection
+ * is exact (every polynomial degree stays below N), so du_hat holds the Chebyshev
+ * coefficients of the derivative: the basis stencil of the space (Eq. fast_shen) maps u_hat
+ * to Chebyshev coefficients, then
+ *   axis 0         the Chebyshev derivative recurrence  c_k b_k = b_{k+2} + 2(k+1) a_{k+1}
+ *                  (c_0 = 2, c_k = 1 otherwise), applied `order` times;
+ *   Fourier axis   the factor (i k)^order, k = 2 pi l / L with the stored wavenumber l
+ *                  (FFT order; an even-length C2C axis stores the Nyquist mode as l = -M/2, an
+ *                  R2C axis as l = +M/2).
+ *   u_hat   spectral array of this space (rows past the basis size are ignored);
+ *   du_hat  spectral array of the same shape and type (output, all N rows written).
+ * 0 <= axis < ndim and 0 <= order <= 4, else SGM_ERR_ARG.  Out of place only (SGM_ERR_ALIAS).
+ * SGM_F32 spaces compute in FP32 pairs (hi + lo, error-free products and sums) and round
+ * once; SGM_F64 spaces compute in FP64.
+ */
+int sgm_project_dx(sgm_space* space, int axis, int order, const void* u_hat, void* du_hat,
+                   void* stream);
+
 /* ---- complex Ginzburg-Landau equation (Sec. 6 of the paper) ------------------------------- */
 #define SGM_GL_RK4 0      /* explicit classical RK4, the paper's time loop */
 #define SGM_GL_IFRK4 1    /* classical RK4 on exp(-L t) u_hat (linear part integrated exactly) */

@@ -1,0 +1,317 @@
+// project.cu - projected derivatives, project(Dx(u, axis, m), W0) of Sec. 5 of the paper:
+// the kernel, its coefficient table and the C ABI entry point sgm_project_dx.
+//
+// W0 is the space of u with axis 0 replaced by the regular Chebyshev basis (the space itself
+// when all axes are Fourier axes).  Every polynomial degree involved stays below N and
+// Gauss-Chebyshev quadrature with N points integrates degree 2N - 1 exactly, so the Galerkin
+// projection onto W0 of the derivative of u = sum_l u_hat_l phi_l is the Chebyshev expansion
+// of the derivative itself:
+//   1. basis stencil, the Shen-to-Chebyshev map of Eq. fast_shen:
+//        a_q = u_hat_q + beta_{q-2} u_hat_{q-2} + gamma_{q-4} u_hat_{q-4},
+//      Dirichlet beta = -1, gamma = 0; biharmonic beta_j = -2(j+2)/(j+3), gamma_j = (j+1)/(j+3)
+//      (Eq. chebbiharmonic); regular Chebyshev a = u_hat.  Rows of u_hat at or past the basis
+//      size read as zero;
+//   2. a derivative along axis 0 applies the Chebyshev derivative recurrence m times:
+//        c_k b_k = b_{k+2} + 2(k+1) a_{k+1},  c_0 = 2, c_k = 1 (k > 0),  b_N = b_{N+1} = 0;
+//   3. a derivative along a Fourier axis multiplies by (i k)^m, k = 2 pi l / L with the stored
+//      wavenumber l (FFT order; an R2C axis keeps l = 0..M/2).
+//
+// Work split.  Level j (the j-th derivative) at row r uses level j at row r + 2 and level j-1
+// at row r + 1, so the output rows of one parity depend only on the input rows of the other
+// parity (odd m) or the same parity (even m).  One thread takes one column (both components
+// of a complex column) and one output parity, and sweeps its rows downwards: at output row k
+// it holds level j at row k + m - j for every j, plus one previous value per level.  A warp
+// covers 32 adjacent columns, so each row it reads or writes is one contiguous segment.
+// Input rows stream through registers in chunks of kChunk rows, the next chunk's loads issued
+// before the current chunk is consumed.
+//
+// Arithmetic.  FP64 spaces use plain FP64.  FP32 spaces carry every intermediate as an
+// unevaluated pair of floats hi + lo, using Dekker's error-free product (one FMA) and Knuth's
+// two-sum (Dekker 1971, "A floating-point technique for extending the available precision").
+// The result is therefore rounded to FP32 once, and the FP64 pipe (1/64 of the FP32 rate on
+// this GPU) stays idle.
+#include <cmath>
+#include <vector>
+
+#include "space_internal.cuh"
+
+namespace sgm {
+namespace {
+
+constexpr int kChunk = 8;     // input rows per register chunk
+constexpr int kMaxOrder = 4;  // largest derivative order
+constexpr int kThreads = 128;
+
+// Fourier-axis factor of a derivative along axis d: the column index c of the kernel runs
+// over the axes after the Chebyshev axis (all axes of a Fourier-only space) in C order, so
+// the axis-d index is (c / inner) % n.
+struct FourierDx {
+  long inner;    // product of the stored extents of the axes after d
+  int n;         // stored extent of axis d
+  int M;         // transform length of axis d
+  int r2c;       // axis d is R2C (index = wavenumber)
+  int order;     // m
+  double scale;  // 2 pi / L_d
+};
+
+template <typename T> struct Pair { T hi, lo; };
+
+// ---- error-free transforms in FP32 (round-to-nearest intrinsics, never contracted) ----------
+__device__ __forceinline__ Pair<float> two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+// requires |a| >= |b| (or a = 0)
+__device__ __forceinline__ Pair<float> fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+// a + b
+__device__ __forceinline__ Pair<float> padd(Pair<float> a, Pair<float> b) {
+  const Pair<float> s = two_sum(a.hi, b.hi);
+  return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ Pair<double> padd(Pair<double> a, Pair<double> b) { return {a.hi + b.hi, 0.0}; }
+
+// c * a
+__device__ __forceinline__ Pair<float> pmul(Pair<float> c, Pair<float> a) {
+  const float p = __fmul_rn(c.hi, a.hi);
+  const float e = __fmaf_rn(c.hi, a.hi, -p);                         // c.hi a.hi = p + e exactly
+  return fast_two_sum(p, __fmaf_rn(c.hi, a.lo, __fmaf_rn(c.lo, a.hi, e)));
+}
+__device__ __forceinline__ Pair<double> pmul(Pair<double> c, Pair<double> a) { return {c.hi * a.hi, 0.0}; }
+
+template <typename T> __device__ __forceinline__ Pair<T> pval(T x) { return {x, T(0)}; }
+template <typename T> __device__ __forceinline__ Pair<T> phalf(Pair<T> a) { return {a.hi * T(0.5), a.lo * T(0.5)}; }
+
+// one input row of one column: R components, zero outside 0 <= r < nb
+template <typename T, int R>
+__device__ __forceinline__ void load_row(const T* __restrict__ src, long stride, int r, int nb, T (&v)[R]) {
+  if (r >= 0 && r < nb) {
+    if constexpr (R == 2) {
+      const cplx<T> c = *reinterpret_cast<const cplx<T>*>(src + (long)r * stride);
+      v[0] = c.x;
+      v[1] = c.y;
+    } else {
+      v[0] = src[(long)r * stride];
+    }
+  } else {
+#pragma unroll
+    for (int l = 0; l < R; ++l) v[l] = T(0);
+  }
+}
+
+// T: float or double.  R: 1 (the real spectral array of a 1-D Chebyshev space) or 2 (complex).
+// M0: derivative order along the Chebyshev axis.  FAX: multiply by the Fourier factor
+// (i k)^m of fx (then M0 = 0).  tab: per row j the stencil coefficients (beta_j hi, beta_j lo,
+// gamma_j hi, gamma_j lo); NULL for a Fourier-only space, which has one row (N = nb = 1).
+// Grid: x covers the columns, y the two output parities.
+template <typename T, int R, int M0, bool FAX>
+__global__ void __launch_bounds__(kThreads)
+k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long ncols, const T* __restrict__ tab,
+             FourierDx fx) {
+  const long col = (long)blockIdx.x * kThreads + threadIdx.x;
+  const int par = (int)blockIdx.y;
+  if (col >= ncols) return;
+  const int ktop = ((N - 1) & 1) == par ? N - 1 : N - 2;  // highest output row of this parity
+  if (ktop < 0) return;
+  const long stride = ncols * R;  // elements per row
+  const T* src = in + col * R;
+  T* dst = out + col * R;
+
+  Pair<T> K = pval<T>(T(1));
+  int rot = 0;
+  if constexpr (FAX) {
+    const int idx = (int)((col / fx.inner) % fx.n);
+    const double kk = fx.scale * (double)signed_wavenumber(idx, fx.M, fx.r2c);
+    double kd = 1.0;
+    for (int j = 0; j < fx.order; ++j) kd *= kk;
+    K.hi = (T)kd;
+    K.lo = (T)(kd - (double)K.hi);
+    rot = fx.order & 3;
+  }
+
+  // lev[j][l], j >= 1: level j of component l at row (k + M0 - j) + 2, i.e. its previous value
+  Pair<T> lev[M0 + 1][R];
+#pragma unroll
+  for (int j = 0; j <= M0; ++j)
+#pragma unroll
+    for (int l = 0; l < R; ++l) lev[j][l] = pval<T>(T(0));
+
+  // window of u_hat rows (q + 2, q, q - 2) before step q shifts in row q - 4
+  const int qtop = ktop + M0;
+  T w[3][R];
+  load_row<T, R>(src, stride, qtop + 2, nb, w[0]);
+  load_row<T, R>(src, stride, qtop, nb, w[1]);
+  load_row<T, R>(src, stride, qtop - 2, nb, w[2]);
+  T buf[kChunk][R], nxt[kChunk][R];
+  int row = qtop - 4;  // input row consumed by the next step
+#pragma unroll
+  for (int i = 0; i < kChunk; ++i) load_row<T, R>(src, stride, row - 2 * i, nb, buf[i]);
+
+  for (int k0 = ktop; k0 >= 0; k0 -= 2 * kChunk) {
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) load_row<T, R>(src, stride, row - 2 * (kChunk + i), nb, nxt[i]);
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i) {
+      const int k = k0 - 2 * i;
+      if (k < 0) break;
+      const int q = k + M0;  // row of level 0 at this step
+#pragma unroll
+      for (int l = 0; l < R; ++l) {
+        w[0][l] = w[1][l];
+        w[1][l] = w[2][l];
+        w[2][l] = buf[i][l];
+      }
+      Pair<T> be = pval<T>(T(0)), ga = pval<T>(T(0));
+      if (q >= 2 && q - 2 < nb) be = Pair<T>{tab[4 * (q - 2)], tab[4 * (q - 2) + 1]};
+      if (q >= 4 && q - 4 < nb) ga = Pair<T>{tab[4 * (q - 4) + 2], tab[4 * (q - 4) + 3]};
+      T o[R];
+#pragma unroll
+      for (int l = 0; l < R; ++l) {
+        // level 0: Chebyshev coefficient a_q (the basis stencil)
+        Pair<T> cur = padd(padd(pval<T>(w[0][l]), pmul(be, pval<T>(w[1][l]))), pmul(ga, pval<T>(w[2][l])));
+        // level j at row r = q - j: b_r = b_{r+2} + 2 (r + 1) (level j-1 at row r + 1)
+#pragma unroll
+        for (int j = 1; j <= M0; ++j) {
+          const Pair<T> v = padd(lev[j][l], pmul(pval<T>(T(2 * (q - j + 1))), cur));
+          lev[j][l] = v;
+          cur = v;
+        }
+        if (M0 >= 1 && k == 0) cur = phalf(cur);  // c_0 = 2
+        if constexpr (FAX) cur = pmul(K, cur);
+        o[l] = cur.hi;
+      }
+      if constexpr (FAX && R == 2) {  // times i^m
+        const T x = o[0], y = o[1];
+        if (rot == 1) {
+          o[0] = -y;
+          o[1] = x;
+        } else if (rot == 2) {
+          o[0] = -x;
+          o[1] = -y;
+        } else if (rot == 3) {
+          o[0] = y;
+          o[1] = -x;
+        }
+      }
+      if constexpr (R == 2)
+        *reinterpret_cast<cplx<T>*>(dst + (long)k * stride) = mk<cplx<T>>(o[0], o[1]);
+      else
+        dst[(long)k * stride] = o[0];
+    }
+    row -= 2 * kChunk;
+#pragma unroll
+    for (int i = 0; i < kChunk; ++i)
+#pragma unroll
+      for (int l = 0; l < R; ++l) buf[i][l] = nxt[i][l];
+  }
+}
+
+template <typename T, int R, int M0, bool FAX>
+cudaError_t launch_one(const void* in, void* out, int N, int nb, long ncols, const void* tab, const FourierDx& fx,
+                       cudaStream_t s) {
+  const dim3 grid((unsigned)((ncols + kThreads - 1) / kThreads), 2);
+  k_project_dx<T, R, M0, FAX><<<grid, kThreads, 0, s>>>((const T*)in, (T*)out, N, nb, ncols, (const T*)tab, fx);
+  return cudaGetLastError();
+}
+
+template <typename T, int R>
+cudaError_t launch_project(int m0, bool fax, const void* in, void* out, int N, int nb, long ncols, const void* tab,
+                           const FourierDx& fx, cudaStream_t s) {
+  if (fax) {
+    if constexpr (R == 2) return launch_one<T, 2, 0, true>(in, out, N, nb, ncols, tab, fx, s);
+    return cudaErrorInvalidValue;
+  }
+  switch (m0) {
+    case 0: return launch_one<T, R, 0, false>(in, out, N, nb, ncols, tab, fx, s);
+    case 1: return launch_one<T, R, 1, false>(in, out, N, nb, ncols, tab, fx, s);
+    case 2: return launch_one<T, R, 2, false>(in, out, N, nb, ncols, tab, fx, s);
+    case 3: return launch_one<T, R, 3, false>(in, out, N, nb, ncols, tab, fx, s);
+    case 4: return launch_one<T, R, 4, false>(in, out, N, nb, ncols, tab, fx, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <typename T>
+int upload_table(sgm_space* s, const std::vector<long double>& be, const std::vector<long double>& ga) {
+  const size_t n = be.size();
+  std::vector<T> h(4 * n);
+  for (size_t j = 0; j < n; ++j) {
+    const T bh = (T)be[j], gh = (T)ga[j];
+    h[4 * j] = bh;
+    h[4 * j + 1] = (T)(be[j] - (long double)bh);
+    h[4 * j + 2] = gh;
+    h[4 * j + 3] = (T)(ga[j] - (long double)gh);
+  }
+  cudaError_t e = cudaMalloc(&s->pdx_tab, sizeof(T) * h.size());
+  if (e == cudaSuccess) e = cudaMemcpy(s->pdx_tab, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "derivative stencil table: %s", cudaGetErrorString(e));
+  return SGM_OK;
+}
+
+}  // namespace
+
+int build_project_table(sgm_space* s) {
+  if (!s->cheb) return SGM_OK;
+  const int N = (int)s->n[0];
+  std::vector<long double> be(N, 0.0L), ga(N, 0.0L);
+  for (int j = 0; j < N; ++j) {
+    if (s->kinds[0] == SGM_SHEN_DIRICHLET) {
+      be[j] = -1.0L;
+    } else if (s->kinds[0] == SGM_SHEN_BIHARMONIC) {
+      be[j] = -2.0L * (j + 2) / (long double)(j + 3);
+      ga[j] = (long double)(j + 1) / (long double)(j + 3);
+    }
+  }
+  return s->prec == SGM_F32 ? upload_table<float>(s, be, ga) : upload_table<double>(s, be, ga);
+}
+
+}  // namespace sgm
+
+using namespace sgm;
+
+extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_hat, void* du_hat, void* stream) {
+  const int st = space_check(s);
+  if (st != SGM_OK) return st;
+  if (axis < 0 || axis >= s->ndim) return set_error(SGM_ERR_ARG, "axis %d outside 0..%d", axis, s->ndim - 1);
+  if (order < 0 || order > kMaxOrder) return set_error(SGM_ERR_ARG, "order %d outside 0..%d", order, kMaxOrder);
+  if (!u_hat || !du_hat) return set_error(SGM_ERR_NULL, "NULL data pointer");
+  if (((uintptr_t)u_hat & 15) || ((uintptr_t)du_hat & 15))
+    return set_error(SGM_ERR_ALIGN, "data pointers must be 16-byte aligned");
+  const char* a = (const char*)u_hat;
+  const char* b = (const char*)du_hat;
+  if (a < b + s->spec_bytes && b < a + s->spec_bytes) return set_error(SGM_ERR_ALIAS, "u_hat and du_hat overlap");
+  if (s->cheb && !s->pdx_tab) return set_error(SGM_ERR_STATE, "space has no derivative stencil table");
+
+  const int N = s->cheb ? (int)s->n[0] : 1;
+  int nb = 1;
+  if (s->cheb)
+    nb = s->kinds[0] == SGM_SHEN_DIRICHLET ? N - 2 : s->kinds[0] == SGM_SHEN_BIHARMONIC ? N - 4 : N;
+  const long ncols = s->nspec / N;
+  const bool cheb_axis = s->cheb && axis == 0;
+  const int m0 = cheb_axis ? order : 0;
+  const bool fax = !cheb_axis && order > 0;
+  FourierDx fx{1, 1, 1, 0, 0, 0.0};
+  if (fax) {
+    fx.inner = 1;
+    for (int d = axis + 1; d < s->ndim; ++d) fx.inner *= s->spec[d];
+    fx.n = (int)s->spec[axis];
+    fx.M = (int)s->n[axis];
+    fx.r2c = s->kinds[axis] == SGM_FOURIER_R2C;
+    fx.order = order;
+    fx.scale = 2.0 * 3.14159265358979323846 / (s->dom[2 * axis + 1] - s->dom[2 * axis]);
+  }
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t e;
+  if (s->prec == SGM_F32)
+    e = s->real_spec ? launch_project<float, 1>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<float, 2>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+  else
+    e = s->real_spec ? launch_project<double, 1>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<double, 2>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "project_dx: %s", cudaGetErrorString(e));
+  return SGM_OK;
+}

@@ -456,6 +456,7 @@ void free_space(sgm_space* s) {
   cudaFree(s->scratch);
   cudaFree(s->groups);
   for (void* p : s->tc_img) cudaFree(p);
+  cudaFree(s->pdx_tab);
   s->magic = 0;
   delete s;
 }
@@ -600,6 +601,7 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
     const int N = (int)n[0];
     st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);
     if (st == SGM_OK) st = build_tables(s);
+    if (st == SGM_OK) st = build_project_table(s);
     if (st == SGM_OK && (kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC)) {
       int sms = 0;
       chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");

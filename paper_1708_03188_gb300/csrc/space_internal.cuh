@@ -35,6 +35,7 @@ struct sgm_space {
   int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
   int cheb_tc = 0;           // 1: Chebyshev axis by the tensor-core contraction (k_cheb_tc.cu)
   void* tc_img[3] = {nullptr, nullptr, nullptr};  // contraction matrices per ChebMode
+  void* pdx_tab = nullptr;   // Shen-to-Chebyshev stencil coefficients of sgm_project_dx (project.cu)
 
   size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
   size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
@@ -47,4 +48,7 @@ int need_twf(sgm_space* s, int L, const void** out);
 int space_check(const sgm_space* s);
 // device table of the compile-time FFT engine for length L (caller frees)
 int make_fast_twiddles(int precision, int L, void** out);
+// stencil coefficient table of sgm_project_dx for a space with a Chebyshev axis (project.cu);
+// stored in s->pdx_tab, freed with the space
+int build_project_table(sgm_space* s);
 }  // namespace sgm

@@ -35,6 +35,7 @@ _SIGNATURES = {
     "sgm_biharmonic_solve": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
     "sgm_helmholtz": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
     "sgm_biharmonic": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
+    "sgm_project_dx": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
     "sgm_gl_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _D, _D, _D, _D, ctypes.c_int]),
     "sgm_gl_destroy": (ctypes.c_int, [_VP]),
     "sgm_gl_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -113,6 +114,7 @@ class Space:
         self.kinds = tuple(kinds)
         self.sizes = tuple(int(s) for s in sizes)
         self.precision = precision
+        self.domain = domain
         nd = len(self.kinds)
         k = (ctypes.c_int * nd)(*[KINDS[x] for x in self.kinds])
         n = (ctypes.c_int64 * nd)(*self.sizes)
@@ -201,6 +203,25 @@ class Space:
 
     def biharmonic(self, a, b, c, f, out=None, stream=None):
         return self._run(lib().sgm_biharmonic, f, False, False, out, stream, a, b, c)
+
+    def project_dx(self, u_hat, axis, order, out=None, stream=None):
+        """project(Dx(u, axis, order), W0) (Sec. 5): the coefficients in W0 of the order-th
+        derivative (0..4) along ``axis`` of the Function with coefficients u_hat.  W0 is
+        ``chebyshev_space()``; the result has u_hat's shape and dtype."""
+        self._check(u_hat, self.spectral_shape, self.spectral_dtype, "u_hat")
+        if out is None:
+            out = self.empty_spectral(u_hat.device)
+        self._check(out, self.spectral_shape, self.spectral_dtype, "out")
+        check(lib().sgm_project_dx(self._h, int(axis), int(order), _ptr(u_hat), _ptr(out), _stream(stream)))
+        return out
+
+    def chebyshev_space(self):
+        """W0: this space with axis 0 replaced by the regular Chebyshev basis (a new Space with
+        the same sizes, domain and precision); for a Fourier-only space, a copy of it."""
+        kinds = list(self.kinds)
+        if kinds[0] in ("dirichlet", "biharmonic"):
+            kinds[0] = "chebyshev"
+        return Space(kinds, self.sizes, domain=self.domain, precision=self.precision)
 
 
 GL_SCHEMES = {"rk4": 0, "ifrk4": 1}
