@@ -22,8 +22,8 @@
 // of a complex column) and one output parity, and sweeps its rows downwards: at output row k
 // it holds level j at row k + m - j for every j, plus one previous value per level.  A warp
 // covers 32 adjacent columns, so each row it reads or writes is one contiguous segment.
-// Input rows stream through registers in chunks of kChunk rows, the next chunk's loads issued
-// before the current chunk is consumed.
+// Input rows stream through registers in chunks of kChunk rows (16 FP32, 8 FP64), the next
+// chunk's loads issued before the current chunk is consumed.
 //
 // Arithmetic.  FP64 spaces use plain FP64.  FP32 spaces carry every intermediate as an
 // unevaluated pair of floats hi + lo, using Dekker's error-free product (one FMA) and Knuth's
@@ -38,7 +38,9 @@
 namespace sgm {
 namespace {
 
-constexpr int kChunk = 8;     // input rows per register chunk
+// input rows per register chunk: two chunks are in flight per thread; FP32 pairs leave room for
+// a deeper look-ahead than FP64
+template <typename T> constexpr int kChunkOf = sizeof(T) == 4 ? 16 : 8;
 constexpr int kMaxOrder = 4;  // largest derivative order
 constexpr int kThreads = 128;
 
@@ -117,6 +119,7 @@ k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long 
   if (col >= ncols) return;
   const int ktop = ((N - 1) & 1) == par ? N - 1 : N - 2;  // highest output row of this parity
   if (ktop < 0) return;
+  constexpr int kChunk = kChunkOf<T>;
   const long stride = ncols * R;  // elements per row
   const T* src = in + col * R;
   T* dst = out + col * R;
