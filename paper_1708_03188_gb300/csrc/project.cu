@@ -26,10 +26,11 @@
 // chunk's loads issued before the current chunk is consumed.
 //
 // Arithmetic.  FP64 spaces use plain FP64.  FP32 spaces carry every intermediate as an
-// unevaluated pair of floats hi + lo, using Dekker's error-free product (one FMA) and Knuth's
-// two-sum (Dekker 1971, "A floating-point technique for extending the available precision").
-// The result is therefore rounded to FP32 once, and the FP64 pipe (1/64 of the FP32 rate on
-// this GPU) stays idle.
+// unevaluated pair of floats hi + lo: exact products through one FMA (Dekker 1971, "A
+// floating-point technique for extending the available precision"), Knuth's two-sum, and the
+// errors summed in lo without renormalising (the cascaded sums of Ogita, Rump and Oishi 2005,
+// "Accurate sum and dot product").  The result is as accurate as a computation in about twice
+// FP32 precision rounded once, and the FP64 pipe (1/64 of the FP32 rate on this GPU) stays idle.
 #include <cmath>
 #include <vector>
 
@@ -59,31 +60,52 @@ struct FourierDx {
 template <typename T> struct Pair { T hi, lo; };
 
 // ---- error-free transforms in FP32 (round-to-nearest intrinsics, never contracted) ----------
+// s + e = a + b exactly (Knuth's two-sum)
 __device__ __forceinline__ Pair<float> two_sum(float a, float b) {
   const float s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
 }
-// requires |a| >= |b| (or a = 0)
-__device__ __forceinline__ Pair<float> fast_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+
+// Level 0, the Chebyshev coefficient a_q = w0 + beta w2 + gamma w4 of the basis stencil.  The
+// stencil is where accuracy is decided: phi_l is close to a second difference of Chebyshev
+// polynomials, so derivatives of the coefficients cancel strongly and would amplify a plain
+// FP32 rounding of a_q.  The products with the (hi, lo) coefficients are exact up to the lo
+// terms (Dekker's product via one FMA); the sum is a cascaded two-sum whose errors collect in lo.
+__device__ __forceinline__ Pair<float> stencil(float w0, float w2, float w4, Pair<float> be, Pair<float> ga) {
+  const float p1 = __fmul_rn(be.hi, w2);
+  const float e1 = __fmaf_rn(be.lo, w2, __fmaf_rn(be.hi, w2, -p1));
+  const float p2 = __fmul_rn(ga.hi, w4);
+  const float e2 = __fmaf_rn(ga.lo, w4, __fmaf_rn(ga.hi, w4, -p2));
+  const Pair<float> s1 = two_sum(w0, p1);
+  const Pair<float> s2 = two_sum(s1.hi, p2);
+  return {s2.hi, __fadd_rn(__fadd_rn(s1.lo, s2.lo), __fadd_rn(e1, e2))};
+}
+__device__ __forceinline__ Pair<double> stencil(double w0, double w2, double w4, Pair<double> be, Pair<double> ga) {
+  return {fma(ga.hi, w4, fma(be.hi, w2, w0)), 0.0};
 }
 
-// a + b
-__device__ __forceinline__ Pair<float> padd(Pair<float> a, Pair<float> b) {
-  const Pair<float> s = two_sum(a.hi, b.hi);
-  return two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+// One step of the derivative recurrence, prev + c cur with c = 2(r+1) exact.  The pair stays
+// unnormalised: hi carries the running FP32 sum and lo the exact errors of its products and
+// additions (the cascaded dot product "Dot2" of Ogita, Rump and Oishi, 2005).
+__device__ __forceinline__ Pair<float> level(Pair<float> prev, float c, Pair<float> cur) {
+  const float p = __fmul_rn(c, cur.hi);
+  const float pe = __fmaf_rn(c, cur.hi, -p);
+  const Pair<float> s = two_sum(prev.hi, p);
+  return {s.hi, __fadd_rn(prev.lo, __fadd_rn(s.lo, __fmaf_rn(c, cur.lo, pe)))};
 }
-__device__ __forceinline__ Pair<double> padd(Pair<double> a, Pair<double> b) { return {a.hi + b.hi, 0.0}; }
+__device__ __forceinline__ Pair<double> level(Pair<double> prev, double c, Pair<double> cur) {
+  return {fma(c, cur.hi, prev.hi), 0.0};
+}
 
-// c * a
-__device__ __forceinline__ Pair<float> pmul(Pair<float> c, Pair<float> a) {
-  const float p = __fmul_rn(c.hi, a.hi);
-  const float e = __fmaf_rn(c.hi, a.hi, -p);                         // c.hi a.hi = p + e exactly
-  return fast_two_sum(p, __fmaf_rn(c.hi, a.lo, __fmaf_rn(c.lo, a.hi, e)));
+// the output value (K (hi + lo) for a Fourier-axis factor K = Kh + Kl), rounded once
+__device__ __forceinline__ float round_out(Pair<float> v) { return __fadd_rn(v.hi, v.lo); }
+__device__ __forceinline__ double round_out(Pair<double> v) { return v.hi; }
+__device__ __forceinline__ float scale_out(Pair<float> K, Pair<float> v) {
+  const float p = __fmul_rn(K.hi, v.hi);
+  return __fadd_rn(p, __fmaf_rn(K.hi, v.lo, __fmaf_rn(K.lo, v.hi, __fmaf_rn(K.hi, v.hi, -p))));
 }
-__device__ __forceinline__ Pair<double> pmul(Pair<double> c, Pair<double> a) { return {c.hi * a.hi, 0.0}; }
+__device__ __forceinline__ double scale_out(Pair<double> K, Pair<double> v) { return K.hi * v.hi; }
 
 template <typename T> __device__ __forceinline__ Pair<T> pval(T x) { return {x, T(0)}; }
 template <typename T> __device__ __forceinline__ Pair<T> phalf(Pair<T> a) { return {a.hi * T(0.5), a.lo * T(0.5)}; }
@@ -175,17 +197,19 @@ k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long 
 #pragma unroll
       for (int l = 0; l < R; ++l) {
         // level 0: Chebyshev coefficient a_q (the basis stencil)
-        Pair<T> cur = padd(padd(pval<T>(w[0][l]), pmul(be, pval<T>(w[1][l]))), pmul(ga, pval<T>(w[2][l])));
+        Pair<T> cur = stencil(w[0][l], w[1][l], w[2][l], be, ga);
         // level j at row r = q - j: b_r = b_{r+2} + 2 (r + 1) (level j-1 at row r + 1)
 #pragma unroll
         for (int j = 1; j <= M0; ++j) {
-          const Pair<T> v = padd(lev[j][l], pmul(pval<T>(T(2 * (q - j + 1))), cur));
+          const Pair<T> v = level(lev[j][l], T(2 * (q - j + 1)), cur);
           lev[j][l] = v;
           cur = v;
         }
         if (M0 >= 1 && k == 0) cur = phalf(cur);  // c_0 = 2
-        if constexpr (FAX) cur = pmul(K, cur);
-        o[l] = cur.hi;
+        if constexpr (FAX)
+          o[l] = scale_out(K, cur);
+        else
+          o[l] = round_out(cur);
       }
       if constexpr (FAX && R == 2) {  // times i^m
         const T x = o[0], y = o[1];
