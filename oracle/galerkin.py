@@ -6,8 +6,8 @@ Sec. 3.4.2 of the paper defines, with the discrete inner product of Eq. (quadrat
 and Sec. 4 (biharmonic problem) adds
   bi-harmonic S_ml = (phi_l'''', phi_m)_w^N.
 Row index m is the test function, column index l the trial function.  Each entry
-is the quadrature sum over the N Chebyshev-Gauss points; nothing is taken from a
-closed form.
+is the quadrature sum over the N Gauss points of the basis' family (Chebyshev-Gauss,
+or Legendre-Gauss with weight 1); nothing is taken from a closed form.
 
 For one Fourier column with squared wavenumber kappa2 (Eq. laplace), the weak
 forms of
@@ -27,7 +27,7 @@ from . import quadrature
 @functools.lru_cache(maxsize=32)
 def _matrix(kind, N, q):
     """[m, l] = sum_j phi_m(x_j) w_j phi_l^(q)(x_j), the quadrature of (phi_l^(q), phi_m)_w^N."""
-    x, w = quadrature.gauss_points(N)
+    x, w = quadrature.points(kind, N)
     phi = quadrature.basis_values(kind, N, x, 0)          # (N, nb)
     dphi = quadrature.basis_values(kind, N, x, q)
     m = (phi * w[:, None]).T @ dphi

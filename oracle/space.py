@@ -97,7 +97,7 @@ class Space:
     # ---- Shen part ------------------------------------------------------------------
     def _shen_scalar(self, g):
         kind, N = self.kinds[0], self.sizes[0]
-        x, w = quadrature.gauss_points(N)
+        x, w = quadrature.points(kind, N)
         phi = quadrature.basis_values(kind, N, x)              # (N, nb)
         nb = phi.shape[1]
         s = np.tensordot((phi * w[:, None]).T, g, axes=([1], [0]))
@@ -107,7 +107,7 @@ class Space:
 
     def _shen_backward(self, c):
         kind, N = self.kinds[0], self.sizes[0]
-        x, _ = quadrature.gauss_points(N)
+        x, _ = quadrature.points(kind, N)
         phi = quadrature.basis_values(kind, N, x)
         nb = phi.shape[1]
         return np.tensordot(phi, np.asarray(c)[:nb], axes=([1], [0]))
@@ -148,8 +148,8 @@ class Space:
     def project_dx(self, u_hat, axis, order):
         """project(Dx(u, axis, order), W0) of Sec. 5 for the Function with coefficients u_hat.
 
-        W0 is this space with axis 0 replaced by the regular Chebyshev basis (W0 is the space
-        itself when every axis is a Fourier axis).  The projection onto W0 is the forward
+        W0 is this space with axis 0 replaced by the regular basis of its family, T_k or L_k
+        (W0 is the space itself when every axis is a Fourier axis).  The projection onto W0 is the forward
         transform of Sec. 3.4.2 applied to the derivative, written with Galerkin matrices:
           Chebyshev axis    B0^{-1} C u_hat, with C[k, l] = (d^m phi_l / dx^m, T_k)_w^N and the
                             regular basis' mass matrix B0[k, j] = (T_j, T_k)_w^N, both by
@@ -168,8 +168,8 @@ class Space:
         if self.has_cheb:
             kind, N = self.kinds[0], self.sizes[0]
             m0 = order if axis == 0 else 0
-            x, w = quadrature.gauss_points(N)
-            T = quadrature.basis_values("chebyshev", N, x)        # T_k(x_j), (N, N)
+            x, w = quadrature.points(kind, N)
+            T = quadrature.basis_values(quadrature.regular_kind(kind), N, x)   # T_k (or L_k) at x_j
             V = quadrature.basis_values(kind, N, x, deriv=m0)     # phi_l^(m0)(x_j), (N, nb)
             nb = V.shape[1]
             Tw = T * w[:, None]

@@ -34,6 +34,11 @@ def cheb_points(N):
     return np.cos((2 * j + 1) * np.pi / (2 * N))
 
 
+def legendre_points(N):
+    """Legendre-Gauss sampling points, descending like the Chebyshev points."""
+    return np.polynomial.legendre.leggauss(N)[0][::-1].copy()
+
+
 def fourier_points(M, domain=(0.0, 2 * np.pi)):
     a, b = domain
     return a + (b - a) * np.arange(M, dtype=np.float64) / M
@@ -46,6 +51,8 @@ def mesh(kinds, sizes, domains=None):
     for d, (k, n) in enumerate(zip(kinds, sizes)):
         if k in ("chebyshev", "dirichlet", "biharmonic"):
             x = cheb_points(n)
+        elif k in ("legendre", "legendre_dirichlet", "legendre_biharmonic"):
+            x = legendre_points(n)
         else:
             x = fourier_points(n, (domains[d] if domains else (0.0, 2 * np.pi)))
         shp = [1] * nd
