@@ -69,3 +69,4 @@ def test_null_arguments(libsgm):
     assert libsgm.sgm_space_destroy(None) == 0
     assert libsgm.sgm_scalar_product(None, None, None, None) == -1
     assert libsgm.sgm_helmholtz_solve(None, 1.0, 0.0, None, None, None) == -1
+    assert libsgm.sgm_project_dx(None, 0, 1, None, None, None) == -1
