@@ -17,6 +17,7 @@ workload on rank 0.
 """
 import argparse
 import json
+import math
 import os
 import subprocess
 import sys
@@ -163,6 +164,29 @@ FLOPS_PER_ROW = {"dirichlet": 15 / 2 + 16, "biharmonic": 53 / 4 + 34}
 # one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum)
 BIH_TRAFFIC_BYTES = 309_025_280 + 318_420_736
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); measured 1.19 by an FMA probe
+# FP32 ALU peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum
+# SM clock = 80.5 TFLOP/s
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07 / 1e3
+
+
+def gl_flops_per_step(M):
+    """Algorithmic flops of one RK4 step of the 3/2-padded Ginzburg-Landau right-hand side on an
+    M x M grid.  Per stage: one inverse and one forward 2-D transform at Mp = 3M/2, each pruned to
+    M lines in the pass that touches the zero padding, at 5 L log2 L flops per complex FFT of
+    length L; the cubic term (1 + i gamma)|u|^2 u, 11 flops per padded point; the linear term and
+    the stage combination, 16 flops per retained coefficient.  Four stages per step."""
+    Mp = 3 * M // 2
+    fft = 5 * Mp * math.log2(Mp)
+    per_transform = (M + Mp) * fft
+    return 4 * (2 * per_transform + 11 * Mp * Mp + 16 * M * M)
+
+
+def rel_l2(a, b):
+    """Relative L2 difference of two tensors (computed in complex128 / float64)."""
+    import torch
+    wide = torch.complex128 if (a.is_complex() or b.is_complex()) else torch.float64
+    a, b = a.to(wide), b.to(wide)
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
 
 
 def run_ours(args):
@@ -438,12 +462,18 @@ def project_measure(sp, u_hat, stream, reps=20):
 
 def gl_measure(Space, stream, M=512, steps=200):
     """Ginzburg-Landau steps/s on M x M (Fourier 512^2, [-50,50]^2, 3/2-rule padding, beta=1.5,
-    gamma=-0.5, seeded u0 = 0.01 (N(0,1) + i N(0,1))); steps timed with CUDA events."""
+    gamma=-0.5, seeded u0 = 0.01 (N(0,1) + i N(0,1))); steps timed with CUDA events.  Each line
+    also gives the algorithmic TFLOP/s (gl_flops_per_step) as a fraction of the FP64 or FP32 ALU
+    peak, and the run ends with the complex64 state's relative L2 difference from complex128."""
     import torch
     from paper_1708_03188_gb300 import inputs
     from paper_1708_03188_gb300.sgm import GinzburgLandau
-    out = {"grid": f"{M}^2", "padded": f"{3 * M // 2}^2", "beta": 1.5, "gamma": -0.5}
+    flops = gl_flops_per_step(M)
+    out = {"grid": f"{M}^2", "padded": f"{3 * M // 2}^2", "beta": 1.5, "gamma": -0.5,
+           "gflop_per_step": round(flops / 1e9, 4),
+           "peaks_tflops": {"f64": FP64_PEAK_TFLOPS, "f32": round(FP32_PEAK_TFLOPS, 1)}}
     u0 = inputs.gl_initial(M)
+    final = {}
     for prec in ("f64", "f32"):
         sp = Space(["c2c", "c2c"], (M, M), domain=[(-50.0, 50.0), (-50.0, 50.0)], precision=prec)
         uphys = torch.from_numpy(u0).to(sp.physical_dtype).cuda()
@@ -460,10 +490,17 @@ def gl_measure(Space, stream, M=512, steps=200):
             b.synchronize()
             ms = a.elapsed_time(b) / steps
             finite = bool(torch.isfinite(torch.view_as_real(u)).all().item())
+            tflops = flops / (ms * 1e-3) / 1e12
             out[f"{prec}_{scheme}_dt{dt}"] = {"steps_per_s": round(1e3 / ms, 1), "ms_per_step": round(ms, 5),
-                                              "finite_after": finite, "launches_per_step": 12}
+                                              "finite_after": finite, "launches_per_step": 12,
+                                              "tflops": round(tflops, 3), "bound": "alu",
+                                              "frac": round(tflops / out["peaks_tflops"][prec], 4)}
+            if scheme == "ifrk4":
+                final[prec] = u.clone()
             gl.close()
         sp.close()
+    # complex64 against complex128 from the same initial state after the same 3 + steps steps
+    out["c64_vs_c128"] = {"rel_l2": rel_l2(final["f32"], final["f64"]), "steps": 3 + steps, "scheme": "ifrk4"}
     return out
 
 

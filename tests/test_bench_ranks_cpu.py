@@ -47,3 +47,21 @@ def test_max_over_ranks_gloo():
 def test_single_process_is_identity():
     import bench
     assert bench.max_over_ranks(2.25) == 2.25
+
+
+def test_gl_flop_model_and_rel_l2():
+    import math
+
+    import torch
+
+    import bench
+    # 512^2 grid, 768^2 padded: (512 + 768) * 5 * 768 * log2(768) per transform, two per stage,
+    # plus 11 flops per padded point and 16 per retained coefficient; four stages
+    fft = 5 * 768 * math.log2(768)
+    expect = 4 * (2 * 1280 * fft + 11 * 768 ** 2 + 16 * 512 ** 2)
+    assert abs(bench.gl_flops_per_step(512) - expect) < 1e-6 * expect
+    assert 0.41e9 < bench.gl_flops_per_step(512) < 0.43e9
+    assert abs(bench.FP32_PEAK_TFLOPS - 80.5) < 0.1
+    a = torch.tensor([1 + 1j, 2.0], dtype=torch.complex64)
+    b = torch.tensor([1 + 1j, 2.0 + 1e-3], dtype=torch.complex128)
+    assert abs(bench.rel_l2(a, b) - 1e-3 / math.sqrt(2 + 2.001 ** 2)) < 1e-9
