@@ -561,7 +561,10 @@ def batch_measure(stream, reps=20):
             for sp, (fv, uv) in zip(spaces, views):
                 sp.helmholtz(-1.0, 0.0, fv, out=uv, stream=stream)
         ms_serial = timed(serial)
+        # algorithmic bytes: read f and write u once per point
+        gbs = 2 * (4 if prec == "f32" else 8) * (dof1 + dof2) / (ms * 1e-3) / 1e9
         out[prec] = {"ms_per_batch": round(ms, 4), "gdof_s": round((dof1 + dof2) / (ms * 1e-3) / 1e9, 3),
+                     "gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak()[0], 4),
                      "graph_launches_per_batch": 1,
                      "autotuned_plan": {"bluestein_prime": b.plan[0], "bluestein_problems": b.plan[1]},
                      "default_plan": {"bluestein_prime": 32, "ms_per_batch": round(ms_default, 4),
