@@ -162,8 +162,15 @@ class Space:
     def _check(self, t, shape, dtype, name):
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError(f"{name} must be a CUDA tensor")
-        if tuple(t.shape) != tuple(shape) or t.dtype != dtype or not t.is_contiguous():
-            raise ValueError(f"{name}: expected contiguous {dtype} of shape {shape}, got {t.dtype} {tuple(t.shape)}")
+        wrong = []
+        if tuple(t.shape) != tuple(shape):
+            wrong.append(f"shape {tuple(t.shape)} (expected {tuple(shape)})")
+        if t.dtype != dtype:
+            wrong.append(f"dtype {t.dtype} (expected {dtype})")
+        if not t.is_contiguous():
+            wrong.append(f"strides {tuple(t.stride())} (expected C-contiguous)")
+        if wrong:
+            raise ValueError(f"{name}: " + "; ".join(wrong))
 
     def empty_physical(self, device="cuda"):
         return torch.empty(self.physical_shape, dtype=self.physical_dtype, device=device)

@@ -47,7 +47,7 @@ def test_plane_wave_512(scheme, dt):
     A, om = np.sqrt(1 - k2), beta * k2 + gamma * (1 - k2)
     x = -50 + 100 * np.arange(M) / M
     wave = lambda t: A * np.exp(1j * (k0 * (x[:, None] + 50) + k1 * (x[None, :] + 50) - om * t))
-    to_hat = lambda u: fourier.c2c_forward(fourier.c2c_forward(u, 0), 1)
+    to_hat = lambda u: np.ascontiguousarray(fourier.c2c_forward(fourier.c2c_forward(u, 0), 1))
     sp, gl = make("f64", dt, scheme)
     u = torch.from_numpy(to_hat(wave(0.0))).cuda()
     n = int(round(T / dt))
