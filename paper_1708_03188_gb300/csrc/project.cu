@@ -303,6 +303,7 @@ using namespace sgm;
 extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_hat, void* du_hat, void* stream) {
   const int st = space_check(s);
   if (st != SGM_OK) return st;
+  if (s->legendre) return set_error(SGM_ERR_SIZE, "projected derivatives are not implemented for Legendre bases");
   if (axis < 0 || axis >= s->ndim) return set_error(SGM_ERR_ARG, "axis %d outside 0..%d", axis, s->ndim - 1);
   if (order < 0 || order > kMaxOrder) return set_error(SGM_ERR_ARG, "order %d outside 0..%d", order, kMaxOrder);
   if (!u_hat || !du_hat) return set_error(SGM_ERR_NULL, "NULL data pointer");
