@@ -202,8 +202,10 @@ int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f
 /*
  * Projected derivative, project(Dx(u, axis, order), W0) of Sec. 5: the coefficients in W0 of
  * the order-th partial derivative along `axis` of the Function u whose coefficients in this
- * space are u_hat.  W0 is this space with axis 0 replaced by SGM_CHEBYSHEV (same sizes, domain
- * and precision); when every axis is a Fourier axis, W0 is this space itself.  The projection
+ * space are u_hat.  W0 is this space with axis 0 replaced by SGM_CHEBYSHEV, or by SGM_LEGENDRE for
+ * the Legendre bases (same sizes, domain and precision); when every axis is a Fourier axis, W0 is
+ * this space itself.  Legendre bases use the Legendre derivative recurrence
+ * b_r / (2r+1) = b_{r+2} / (2r+5) + a_{r+1} in place of the Chebyshev one below.  The projection
  * is exact (every polynomial degree stays below N), so du_hat holds the Chebyshev
  * coefficients of the derivative: the basis stencil of the space (Eq. fast_shen) maps u_hat
  * to Chebyshev coefficients, then

@@ -621,6 +621,7 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   chk(cudaMalloc(&s->W2, (size_t)s->nspec * 16), "workspace");
   if (st == SGM_OK && legendre) {
     st = legendre_build(s);
+    if (st == SGM_OK) st = build_project_table(s);
   } else if (st == SGM_OK && cheb) {
     const int N = (int)n[0];
     st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);

@@ -145,5 +145,4 @@ def test_legendre_errors():
     x = torch.zeros(gs.spectral_shape, dtype=gs.spectral_dtype, device="cuda")
     with pytest.raises(SgmError):
         gs.helmholtz_solve(-1.0, 0.0, x)
-    with pytest.raises(SgmError):
-        gs.project_dx(x, 0, 1)
+    assert gs.chebyshev_space().kinds == ("legendre", "c2c")
