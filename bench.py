@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--gl-steps", type=int, default=200,
                    help="time this many Ginzburg-Landau steps per variant (0: skip)")
     p.add_argument("--kernel", default=None,
-                   choices=["helmholtz_solve", "biharmonic_solve", "scalar_product", "backward", "step"],
+                   choices=["helmholtz_solve", "biharmonic_solve", "scalar_product", "backward", "step",
+                            "project_dx"],
                    help="run only this call (warmup + steps times) for profiling; prints no bench line")
     return p.parse_args()
 
@@ -244,6 +245,7 @@ def run_ours(args):
                  "biharmonic_solve": lambda: sp_b.biharmonic_solve(1.0, 0.0, 0.0, rhs_b, out=work),
                  "scalar_product": lambda: sp_b.scalar_product(f_b, out=work),
                  "backward": lambda: sp_b.backward(rhs_b, out=u_b),
+                 "project_dx": lambda: sp_b.project_dx(rhs_b, 0, 1, out=work),
                  "step": step}
         for _ in range(args.warmup + args.steps):
             calls[args.kernel]()

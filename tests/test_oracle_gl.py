@@ -74,7 +74,8 @@ def test_padded_product_equals_modular_convolution(M, factor):
     # wrapped terms are exactly those the padded mesh aliases.
     g = np.random.default_rng(1)
     uh = g.standard_normal((M, M)) + 1j * g.standard_normal((M, M))
-    Mp = gl.padded_size(M, factor)
+    Mp = {1.5: 3 * M // 2, 2.0: 2 * M}[factor]           # the 3/2 rule's mesh (Sec. 6), or 2M
+    assert gl.padded_size(M, factor) == Mp
     got = gl.nonlinear(uh, 0.0, factor)
     l = fourier.wavenumbers(M).astype(int)
     acc = {}
