@@ -108,8 +108,9 @@ const char* sgm_status_string(int status);
  *              and [0, 2 pi) on a Fourier axis.  A Fourier axis of length L = hi - lo is
  *              mapped onto [0, 2 pi), so its derivatives scale by 2 pi / L (Sec. 6).
  *              A Chebyshev or Legendre axis must keep [-1, 1].
- *   precision  SGM_F32 or SGM_F64.  An SGM_F32 space with a Chebyshev axis of N <= 128
- *              points may add one Chebyshev-axis method flag:
+ *   precision  SGM_F32 or SGM_F64.  An SGM_F32 space with a Chebyshev or Legendre axis of
+ *              N <= 128 points may add one axis-0 method flag (for a Legendre axis the
+ *              alternative to the tensor cores is its dense CUDA-core product, not an FFT):
  *                SGM_CHEB_TC    the Chebyshev-axis scalar product, forward T_k transform and
  *                               backward transform run as one dense N x N contraction per
  *                               column on the tensor cores (tcgen05, BF16x3 split products,

@@ -14,7 +14,9 @@
 //   backward         P[j][k] = phi_k(x_j)                   columns past the basis are zero
 //   forward (L_k)    P[k][j] = (2k+1)/2 w_j L_k(x_j)         the mass matrix is diag(2/(2k+1))
 // k_dense_axis0 is a tiled product: a 64 x 64 output tile per CTA, 16-deep slices of P and X
-// staged in shared memory, 4 x 4 outputs per thread, accumulated in the space's precision.
+// staged in shared memory, 4 x 4 outputs per thread, accumulated in the space's precision.  FP32
+// spaces of N <= 128 created with SGM_CHEB_TC or SGM_CHEB_AUTO can run the same products on the
+// tensor cores instead: the images of these matrices feed the BF16x3 contraction of k_cheb_tc.cu.
 //
 // Solves.  With weight 1 the weak forms integrate by parts, (phi_l'', phi_m) = -(phi_l', phi_m')
 // and (phi_l'''', phi_m) = (phi_l'', phi_m''), and the derivatives of the bases have one or two
@@ -356,7 +358,7 @@ cudaError_t launch_dense(const void* P, const void* in, void* out, int N, long C
 
 }  // namespace
 
-int legendre_build(sgm_space* s) {
+int legendre_build(sgm_space* s, bool tc_images) {
   const int N = (int)s->n[0], kind = s->kinds[0];
   if (N > kLegMaxN) return set_error(SGM_ERR_SIZE, "Legendre bases need N <= %d (got %d)", kLegMaxN, N);
   const auto mats = dense_matrices(kind, N);
@@ -365,6 +367,12 @@ int legendre_build(sgm_space* s) {
     const int st = s->prec == SGM_F32 ? upload<float>(mats[mode], &s->leg_mat[mode])
                                       : upload<double>(mats[mode], &s->leg_mat[mode]);
     if (st != SGM_OK) return st;
+    if (tc_images && s->prec == SGM_F32 && N <= kTcMaxN) {  // BF16x3 contraction images (k_cheb_tc.cu)
+      const std::vector<uint16_t> img = tc_matrix_image(mats[mode], N);
+      cudaError_t e = cudaMalloc(&s->tc_img[mode], img.size() * 2);
+      if (e == cudaSuccess) e = cudaMemcpy(s->tc_img[mode], img.data(), img.size() * 2, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "Legendre contraction matrix: %s", cudaGetErrorString(e));
+    }
   }
   if (kind == SGM_LEGENDRE) return SGM_OK;  // no solves on the regular basis
   const std::vector<double> band = band_table(kind, N);

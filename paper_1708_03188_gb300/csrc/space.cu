@@ -359,8 +359,8 @@ int cheb_pass_tc(sgm_space* s, int mode, const void* in, void* out, cudaStream_t
 template <typename T>
 int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide = false) {
   const int N = (int)s->n[0];
-  if (s->legendre) return legendre_pass(s, mode, in, out, st, wide);
   if (sizeof(T) == 4 && s->cheb_tc) return cheb_pass_tc(s, mode, in, out, st, wide);
+  if (s->legendre) return legendre_pass(s, mode, in, out, st, wide);
   long inner = 1;
   for (int i = 1; i < s->ndim; ++i) inner *= s->spec[i];
   FftPlan p = make_plan(N);
@@ -569,7 +569,6 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (kinds[0] == SGM_LEGENDRE_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "Legendre biharmonic basis needs N >= 6");
   // the Legendre transforms are dense N x N matrices held by the space
   if (legendre && n[0] > 1024) return fail(SGM_ERR_SIZE, "Legendre bases need N <= 1024 (got %lld)", (long long)n[0]);
-  if (legendre && cheb_flags) return fail(SGM_ERR_ARG, "Chebyshev-axis method flags need a Chebyshev axis");
   if (kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] < 2) return fail(SGM_ERR_SIZE, "R2C axis needs M >= 2");
   if ((cheb_flags & SGM_CHEB_TC) && (!cheb || n[0] > kTcMaxN))
     return fail(SGM_ERR_SIZE, "SGM_CHEB_TC needs a Chebyshev axis of at most %d points", kTcMaxN);
@@ -620,7 +619,7 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   // W2 holds the spectral intermediate of the physical-to-physical solves, in FP64
   chk(cudaMalloc(&s->W2, (size_t)s->nspec * 16), "workspace");
   if (st == SGM_OK && legendre) {
-    st = legendre_build(s);
+    st = legendre_build(s, cheb_flags != 0 && n[0] <= kTcMaxN);
     if (st == SGM_OK) st = build_project_table(s);
   } else if (st == SGM_OK && cheb) {
     const int N = (int)n[0];
@@ -664,9 +663,11 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
     }
   }
-  if (st == SGM_OK && cheb && !legendre && cheb_flags && n[0] <= kTcMaxN) {
+  if (st == SGM_OK && cheb && cheb_flags && n[0] <= kTcMaxN) {
     const int N = (int)n[0];
+    // a Legendre space got the images of its dense matrices from legendre_build
     for (int mode : {kChebScalar, kChebBackward, kChebForwardT}) {
+      if (legendre) continue;
       const std::vector<uint16_t> img = tc_cheb_image(mode, kinds[0], N);
       chk(cudaMalloc(&s->tc_img[mode], img.size() * 2), "contraction matrix");
       if (st == SGM_OK)

@@ -56,12 +56,13 @@ int make_fast_twiddles(int precision, int L, void** out);
 // stencil coefficient table of sgm_project_dx for a space with a Chebyshev axis (project.cu);
 // stored in s->pdx_tab, freed with the space
 int build_project_table(sgm_space* s);
-// Legendre axis 0 (legendre.cu): tables, matrices and solve scratch of a new space (freed with
+// Legendre axis 0 (legendre.cu): tables, matrices and solve scratch of a new space, plus the
+// tensor-core images of its matrices in s->tc_img when tc_images (FP32, N <= 128; all freed with
 // the space); one axis-0 pass (mode: ChebMode; wide: the spectral side is FP64 on an FP32 space);
 // the banded FP64 solve of a (S - 2 k2 A + k2^2 B) + b (A - k2 B) + c B, the biharmonic weak form
 // (a Dirichlet problem a lap(u) + b u = f is (0, a, b): its tables have S = 0), on spectral data
 // of type TS (float or double)
-int legendre_build(sgm_space* s);
+int legendre_build(sgm_space* s, bool tc_images);
 int legendre_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide);
 template <typename TS>
 int legendre_solve(sgm_space* s, double a, double b, double c, const void* in, void* out, const Wavenumbers& wn,

@@ -144,10 +144,13 @@ class Space:
 
     @property
     def cheb_method(self):
-        """"tc" if the Chebyshev axis runs as the tensor-core contraction, else "fft"."""
+        """"tc" if axis 0 runs as the tensor-core contraction, else "fft" (Chebyshev: DCT via FFT)
+        or "dense" (Legendre: the dense CUDA-core product)."""
         m = ctypes.c_int()
         check(lib().sgm_space_cheb_method(self._h, ctypes.byref(m)))
-        return "tc" if m.value else "fft"
+        if m.value:
+            return "tc"
+        return "dense" if self.kinds[0].startswith("legendre") else "fft"
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

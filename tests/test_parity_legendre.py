@@ -138,7 +138,9 @@ def test_legendre_errors():
     with pytest.raises(SgmError):
         Space(["legendre_dirichlet", "r2c"], [1025, 8], precision="f64")
     with pytest.raises(SgmError):
-        Space(["legendre_dirichlet", "r2c"], [32, 8], precision="f32", cheb="tc")
+        Space(["legendre_dirichlet", "r2c"], [129, 8], precision="f32", cheb="tc")   # N <= 128 on the tensor cores
+    with pytest.raises(SgmError):
+        Space(["legendre_dirichlet", "r2c"], [32, 8], precision="f64", cheb="tc")
     with pytest.raises(SgmError):
         Space(["c2c", "legendre"], [8, 8], precision="f64")
     gs = gspace(["legendre_biharmonic", "c2c"], [16, 8], "f64")
@@ -146,3 +148,36 @@ def test_legendre_errors():
     with pytest.raises(SgmError):
         gs.helmholtz_solve(-1.0, 0.0, x)
     assert gs.chebyshev_space().kinds == ("legendre", "c2c")
+
+
+TOL_TC = 2.0 ** -16      # BF16x3 split products, FP32 accumulation (as for the Chebyshev contraction)
+
+
+@pytest.mark.parametrize("kinds,sizes", [(["legendre"], [2]), (["legendre_dirichlet"], [128]),
+                                         (["legendre_biharmonic", "r2c"], [64, 126]),
+                                         (["legendre_dirichlet", "c2c", "r2c"], [33, 12, 30])],
+                         ids=lambda v: "-".join(map(str, v)))
+def test_legendre_tensor_core_transforms(kinds, sizes):
+    from paper_1708_03188_gb300.sgm import Space
+    gs = Space(kinds, sizes, precision="f32", cheb="tc")
+    assert gs.cheb_method == "tc"
+    os_ = OSpace(kinds, sizes)
+    g = inputs.rng("box3d", 870 + sizes[0])
+    x = g.standard_normal(gs.physical_shape)
+    if not gs.real_physical:
+        x = x + 1j * g.standard_normal(gs.physical_shape)
+    xd = to_dev(x, gs.physical_dtype)
+    xo = to_np(xd)
+    assert rel(to_np(gs.scalar_product(xd)), os_.scalar_product(xo)) < TOL_TC
+    cond = 1.0 if kinds[0] == "legendre" else np.linalg.cond(os_.matrices()["B"])
+    assert rel(to_np(gs.forward(xd)), os_.forward(xo)) < TOL_TC * max(1.0, cond)
+    nb = quadrature.num_basis(kinds[0], sizes[0])
+    c = g.standard_normal(gs.spectral_shape)
+    if not gs.real_spectral:
+        c = c + 1j * g.standard_normal(gs.spectral_shape)
+    c[nb:] = 0
+    c = os_.forward(os_.backward(c))
+    cd = to_dev(c, gs.spectral_dtype)
+    assert rel(to_np(gs.backward(cd)), os_.backward(to_np(cd))) < TOL_TC
+    auto = Space(kinds, sizes, precision="f32", cheb="auto")
+    assert auto.cheb_method in ("tc", "dense")
