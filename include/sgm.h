@@ -20,9 +20,9 @@
  *
  * Data layout (Sec. 4 of the paper; the default axis order of its TensorProductSpace)
  * -------------------------------------------------------------------------------
- *  A space has ndim axes.  Either axis 0 is a Chebyshev axis (SGM_CHEBYSHEV,
- *  SGM_SHEN_DIRICHLET or SGM_SHEN_BIHARMONIC) and axes 1.. are Fourier axes, or all
- *  axes are Fourier axes.  Only the last axis may be SGM_FOURIER_R2C.
+ *  A space has ndim axes.  Either axis 0 is a polynomial axis (SGM_CHEBYSHEV,
+ *  SGM_SHEN_DIRICHLET, SGM_SHEN_BIHARMONIC, or the Legendre bases SGM_LEGENDRE*) and axes 1..
+ *  are Fourier axes, or all axes are Fourier axes.  Only the last axis may be SGM_FOURIER_R2C.
  *  Physical arrays have shape (n[0], ..., n[ndim-1]); they are real when the last
  *  axis is R2C or the space is one Chebyshev axis alone, complex otherwise.
  *  Spectral arrays are complex (interleaved re, im) of shape (n[0], ..., m) with
@@ -69,6 +69,14 @@ extern "C" {
 #define SGM_SHEN_BIHARMONIC 2    /* T_k - 2(k+2)/(k+3) T_{k+2} + (k+1)/(k+3) T_{k+4}, k = 0..N-5 (Eq. chebbiharmonic) */
 #define SGM_FOURIER_C2C 3        /* exp(i l x), complex data */
 #define SGM_FOURIER_R2C 4        /* exp(i l x), real data, l = 0..M/2 stored (last axis only) */
+/* Legendre bases (Sec. 3.1; Eq. legdirichlet; Eq. legbiharmonic with the factor L_{k+4} of its last
+ * term, which the printed formula lacks and phi(+-1) = phi'(+-1) = 0 requires), axis 0 only,
+ * 2 <= N <= 1024, on the Legendre-Gauss points in descending order (weight 1).  Their
+ * transforms are dense O(N^2) sums (no fast transform is known, Sec. 3.4.2); their Helmholtz and
+ * biharmonic systems are banded within a parity after integration by parts. */
+#define SGM_LEGENDRE 5             /* L_k, k = 0..N-1 */
+#define SGM_LEGENDRE_DIRICHLET 6   /* L_k - L_{k+2}, k = 0..N-3 */
+#define SGM_LEGENDRE_BIHARMONIC 7  /* L_k - 2(2k+5)/(2k+7) L_{k+2} + (2k+3)/(2k+7) L_{k+4}, k = 0..N-5 */
 
 /* precision */
 #define SGM_F32 1                /* FP32 transforms, FP64 eliminations */
@@ -94,13 +102,15 @@ const char* sgm_status_string(int status);
  *   ndim       1..3.
  *   kinds      ndim basis kinds (see above).
  *   n          ndim sizes: quadrature points per axis (N >= 4 for Dirichlet, 6 <= N <= 2048
- *              for biharmonic; Fourier sizes >= 1).  Every size <= 4096.
+ *              for biharmonic, N <= 1024 for the Legendre bases; Fourier sizes >= 1).  Every
+ *              size <= 4096.
  *   domain     2*ndim doubles (lo, hi) per axis, or NULL for [-1,1] on a Chebyshev axis
  *              and [0, 2 pi) on a Fourier axis.  A Fourier axis of length L = hi - lo is
  *              mapped onto [0, 2 pi), so its derivatives scale by 2 pi / L (Sec. 6).
- *              A Chebyshev axis must keep [-1, 1].
- *   precision  SGM_F32 or SGM_F64.  An SGM_F32 space with a Chebyshev axis of N <= 128
- *              points may add one Chebyshev-axis method flag:
+ *              A Chebyshev or Legendre axis must keep [-1, 1].
+ *   precision  SGM_F32 or SGM_F64.  An SGM_F32 space with a Chebyshev or Legendre axis of
+ *              N <= 128 points may add one axis-0 method flag (for a Legendre axis the
+ *              alternative to the tensor cores is its dense CUDA-core product, not an FFT):
  *                SGM_CHEB_TC    the Chebyshev-axis scalar product, forward T_k transform and
  *                               backward transform run as one dense N x N contraction per
  *                               column on the tensor cores (tcgen05, BF16x3 split products,
@@ -162,7 +172,8 @@ int sgm_backward(sgm_space* space, const void* u_hat, void* u, void* stream);
  * the weak form of  a lap(u) + b u = f.  A is the stiffness matrix (phi_l'', phi_m)_w and
  * B the mass matrix of Sec. 3.4.2.  Poisson -lap(u) = f is a = -1, b = 0.
  *   f_tilde  spectral right-hand side (S(F(f)));  u_hat  spectral solution.
- * Works in place (f_tilde == u_hat).  Requires axis 0 = SGM_SHEN_DIRICHLET.
+ * Works in place (f_tilde == u_hat).  Requires axis 0 = SGM_SHEN_DIRICHLET or
+ * SGM_LEGENDRE_DIRICHLET (whose A is diagonal, -(4k+6), and B tridiagonal within a parity).
  * a = b = 0, or a system with a zero pivot, gives SGM_ERR_ARG / non-finite output.
  */
 int sgm_helmholtz_solve(sgm_space* space, double a, double b, const void* f_tilde,
@@ -174,7 +185,8 @@ int sgm_helmholtz_solve(sgm_space* space, double a, double b, const void* f_tild
  *     (a (S - 2 kappa^2 A + kappa^4 B) + b (A - kappa^2 B) + c B) u_hat = f_tilde,
  * the weak form of  a lap^2(u) + b lap(u) + c u = f,  S = (phi_l'''', phi_m)_w.
  * The paper's problem lap^2(u) = f is a = 1, b = c = 0.  Works in place.
- * Requires axis 0 = SGM_SHEN_BIHARMONIC.
+ * Requires axis 0 = SGM_SHEN_BIHARMONIC or SGM_LEGENDRE_BIHARMONIC (whose S is diagonal, A
+ * tridiagonal and B pentadiagonal within a parity).
  */
 int sgm_biharmonic_solve(sgm_space* space, double a, double b, double c, const void* f_tilde,
                          void* u_hat, void* stream);
@@ -191,8 +203,10 @@ int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f
 /*
  * Projected derivative, project(Dx(u, axis, order), W0) of Sec. 5: the coefficients in W0 of
  * the order-th partial derivative along `axis` of the Function u whose coefficients in this
- * space are u_hat.  W0 is this space with axis 0 replaced by SGM_CHEBYSHEV (same sizes, domain
- * and precision); when every axis is a Fourier axis, W0 is this space itself.  The projection
+ * space are u_hat.  W0 is this space with axis 0 replaced by SGM_CHEBYSHEV, or by SGM_LEGENDRE for
+ * the Legendre bases (same sizes, domain and precision); when every axis is a Fourier axis, W0 is
+ * this space itself.  Legendre bases use the Legendre derivative recurrence
+ * b_r / (2r+1) = b_{r+2} / (2r+5) + a_{r+1} in place of the Chebyshev one below.  The projection
  * is exact (every polynomial degree stays below N), so du_hat holds the Chebyshev
  * coefficients of the derivative: the basis stencil of the space (Eq. fast_shen) maps u_hat
  * to Chebyshev coefficients, then

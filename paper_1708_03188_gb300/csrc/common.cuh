@@ -116,6 +116,8 @@ constexpr int kTcMaxN = 128;
 int tc_pad16(int n);
 // number of uint16 in the image is 2 * tc_pad16(N)^2
 std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N);
+// the same image of any N x N matrix P (row-major, row = output row), N <= kTcMaxN
+std::vector<uint16_t> tc_matrix_image(const std::vector<long double>& P, int N);
 int tc_timeouts(bool reset);
 int cnn_tc_timeouts(bool reset);   // k_cnn_tc.cu
 

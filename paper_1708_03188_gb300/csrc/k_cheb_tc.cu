@@ -224,24 +224,15 @@ int tc_pad16(int n) { return (n + 15) / 16 * 16; }
 
 // image of P^T (output rows n < Np, input rows kk < Kp) in the K-major core-matrix layout,
 // BF16 hi part followed by the lo part; mode kChebScalar / kChebForwardT / kChebBackward
-std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N) {
+// BF16 hi and lo images of an N x N matrix P (row = output row, column = input row), zero-padded
+// to tc_pad16(N) and laid out in K-major core matrices for k_cheb_tc
+std::vector<uint16_t> tc_matrix_image(const std::vector<long double>& P, int N) {
   const int Kp = tc_pad16(N), Np = tc_pad16(N);
-  const int nb = basis == kDirichlet ? N - 2 : basis == kBiharmonic ? N - 4 : N;
   std::vector<uint16_t> img((size_t)2 * Np * Kp, 0);
   const size_t half = (size_t)Np * Kp;
-  const long double pi = 3.141592653589793238462643383279502884L;
   for (int n = 0; n < Np; ++n)
     for (int kk = 0; kk < Kp; ++kk) {
-      long double v = 0;
-      if (n < N && kk < N) {
-        if (mode == kChebBackward) {  // output row j = n, input row k = kk
-          if (kk < nb) v = shen_phi(basis, kk, n, N);
-        } else if (mode == kChebForwardT) {  // output row k = n, input row j = kk
-          v = cheb_T(n, kk, N) * 2.0L / ((long double)N * (n == 0 ? 2.0L : 1.0L));
-        } else if (n < nb) {
-          v = shen_phi(basis, n, kk, N) * pi / (long double)N;
-        }
-      }
+      const long double v = (n < N && kk < N) ? P[(size_t)n * N + kk] : 0.0L;
       const uint16_t h = bf16_rn((float)v);
       const uint16_t l = bf16_rn((float)((double)v - bf16_to_double(h)));
       const size_t off = ((size_t)(n / 8) * 128 + (size_t)(n % 8) * 16 + (size_t)(kk % 8) * 2 +
@@ -250,6 +241,25 @@ std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N) {
       img[half + off] = l;
     }
   return img;
+}
+
+std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N) {
+  const int nb = basis == kDirichlet ? N - 2 : basis == kBiharmonic ? N - 4 : N;
+  const long double pi = 3.141592653589793238462643383279502884L;
+  std::vector<long double> P((size_t)N * N, 0.0L);
+  for (int n = 0; n < N; ++n)
+    for (int kk = 0; kk < N; ++kk) {
+      long double v = 0;
+      if (mode == kChebBackward) {  // output row j = n, input row k = kk
+        if (kk < nb) v = shen_phi(basis, kk, n, N);
+      } else if (mode == kChebForwardT) {  // output row k = n, input row j = kk
+        v = cheb_T(n, kk, N) * 2.0L / ((long double)N * (n == 0 ? 2.0L : 1.0L));
+      } else if (n < nb) {
+        v = shen_phi(basis, n, kk, N) * pi / (long double)N;
+      }
+      P[(size_t)n * N + kk] = v;
+    }
+  return tc_matrix_image(P, N);
 }
 
 // shared memory of one CTA: the matrix and two X tiles, BF16 hi and lo parts each

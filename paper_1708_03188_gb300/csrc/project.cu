@@ -12,7 +12,9 @@
 //      (Eq. chebbiharmonic); regular Chebyshev a = u_hat.  Rows of u_hat at or past the basis
 //      size read as zero;
 //   2. a derivative along axis 0 applies the Chebyshev derivative recurrence m times:
-//        c_k b_k = b_{k+2} + 2(k+1) a_{k+1},  c_0 = 2, c_k = 1 (k > 0),  b_N = b_{N+1} = 0;
+//        c_k b_k = b_{k+2} + 2(k+1) a_{k+1},  c_0 = 2, c_k = 1 (k > 0),  b_N = b_{N+1} = 0,
+//      or, for the Legendre bases (W0 the regular Legendre basis, the same stencil form with the
+//      Legendre coefficients), b_k / (2k+1) = b_{k+2} / (2k+5) + a_{k+1};
 //   3. a derivative along a Fourier axis multiplies by (i k)^m, k = 2 pi l / L with the stored
 //      wavenumber l (FFT order; an R2C axis keeps l = 0..M/2).
 //
@@ -107,6 +109,13 @@ __device__ __forceinline__ float scale_out(Pair<float> K, Pair<float> v) {
 }
 __device__ __forceinline__ double scale_out(Pair<double> K, Pair<double> v) { return K.hi * v.hi; }
 
+// c (hi + lo) with c an integer-valued T: the product of hi exactly (one FMA), lo rounded
+__device__ __forceinline__ Pair<float> pscale(float c, Pair<float> v) {
+  const float p = __fmul_rn(c, v.hi);
+  return {p, __fmaf_rn(c, v.lo, __fmaf_rn(c, v.hi, -p))};
+}
+__device__ __forceinline__ Pair<double> pscale(double c, Pair<double> v) { return {c * v.hi, 0.0}; }
+
 template <typename T> __device__ __forceinline__ Pair<T> pval(T x) { return {x, T(0)}; }
 template <typename T> __device__ __forceinline__ Pair<T> phalf(Pair<T> a) { return {a.hi * T(0.5), a.lo * T(0.5)}; }
 
@@ -128,11 +137,13 @@ __device__ __forceinline__ void load_row(const T* __restrict__ src, long stride,
 }
 
 // T: float or double.  R: 1 (the real spectral array of a 1-D Chebyshev space) or 2 (complex).
-// M0: derivative order along the Chebyshev axis.  FAX: multiply by the Fourier factor
+// M0: derivative order along axis 0.  LEG: axis 0 is a Legendre basis, whose derivative
+// recurrence is (2r+1)^-1 b_r = (2r+5)^-1 b_{r+2} + a_{r+1}: each level keeps the running sum
+// c_r = c_{r+2} + a_{r+1} and hands b_r = (2r+1) c_r on (no c_0 factor).  FAX: multiply by the Fourier factor
 // (i k)^m of fx (then M0 = 0).  tab: per row j the stencil coefficients (beta_j hi, beta_j lo,
 // gamma_j hi, gamma_j lo); NULL for a Fourier-only space, which has one row (N = nb = 1).
 // Grid: x covers the columns, y the two output parities.
-template <typename T, int R, int M0, bool FAX>
+template <typename T, int R, int M0, bool FAX, bool LEG>
 __global__ void __launch_bounds__(kThreads)
 k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long ncols, const T* __restrict__ tab,
              FourierDx fx) {
@@ -201,11 +212,17 @@ k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long 
         // level j at row r = q - j: b_r = b_{r+2} + 2 (r + 1) (level j-1 at row r + 1)
 #pragma unroll
         for (int j = 1; j <= M0; ++j) {
-          const Pair<T> v = level(lev[j][l], T(2 * (q - j + 1)), cur);
-          lev[j][l] = v;
-          cur = v;
+          if constexpr (LEG) {
+            const Pair<T> c = level(lev[j][l], T(1), cur);
+            lev[j][l] = c;
+            cur = pscale(T(2 * (q - j) + 1), c);
+          } else {
+            const Pair<T> v = level(lev[j][l], T(2 * (q - j + 1)), cur);
+            lev[j][l] = v;
+            cur = v;
+          }
         }
-        if (M0 >= 1 && k == 0) cur = phalf(cur);  // c_0 = 2
+        if (!LEG && M0 >= 1 && k == 0) cur = phalf(cur);  // c_0 = 2
         if constexpr (FAX)
           o[l] = scale_out(K, cur);
         else
@@ -237,29 +254,36 @@ k_project_dx(const T* __restrict__ in, T* __restrict__ out, int N, int nb, long 
   }
 }
 
-template <typename T, int R, int M0, bool FAX>
+template <typename T, int R, int M0, bool FAX, bool LEG>
 cudaError_t launch_one(const void* in, void* out, int N, int nb, long ncols, const void* tab, const FourierDx& fx,
                        cudaStream_t s) {
   const dim3 grid((unsigned)((ncols + kThreads - 1) / kThreads), 2);
-  k_project_dx<T, R, M0, FAX><<<grid, kThreads, 0, s>>>((const T*)in, (T*)out, N, nb, ncols, (const T*)tab, fx);
+  k_project_dx<T, R, M0, FAX, LEG><<<grid, kThreads, 0, s>>>((const T*)in, (T*)out, N, nb, ncols, (const T*)tab, fx);
   return cudaGetLastError();
 }
 
-template <typename T, int R>
-cudaError_t launch_project(int m0, bool fax, const void* in, void* out, int N, int nb, long ncols, const void* tab,
-                           const FourierDx& fx, cudaStream_t s) {
-  if (fax) {
-    if constexpr (R == 2) return launch_one<T, 2, 0, true>(in, out, N, nb, ncols, tab, fx, s);
-    return cudaErrorInvalidValue;
-  }
+template <typename T, int R, bool LEG>
+cudaError_t launch_order(int m0, const void* in, void* out, int N, int nb, long ncols, const void* tab,
+                         const FourierDx& fx, cudaStream_t s) {
   switch (m0) {
-    case 0: return launch_one<T, R, 0, false>(in, out, N, nb, ncols, tab, fx, s);
-    case 1: return launch_one<T, R, 1, false>(in, out, N, nb, ncols, tab, fx, s);
-    case 2: return launch_one<T, R, 2, false>(in, out, N, nb, ncols, tab, fx, s);
-    case 3: return launch_one<T, R, 3, false>(in, out, N, nb, ncols, tab, fx, s);
-    case 4: return launch_one<T, R, 4, false>(in, out, N, nb, ncols, tab, fx, s);
+    case 0: return launch_one<T, R, 0, false, LEG>(in, out, N, nb, ncols, tab, fx, s);
+    case 1: return launch_one<T, R, 1, false, LEG>(in, out, N, nb, ncols, tab, fx, s);
+    case 2: return launch_one<T, R, 2, false, LEG>(in, out, N, nb, ncols, tab, fx, s);
+    case 3: return launch_one<T, R, 3, false, LEG>(in, out, N, nb, ncols, tab, fx, s);
+    case 4: return launch_one<T, R, 4, false, LEG>(in, out, N, nb, ncols, tab, fx, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <typename T, int R>
+cudaError_t launch_project(int m0, bool fax, bool leg, const void* in, void* out, int N, int nb, long ncols,
+                           const void* tab, const FourierDx& fx, cudaStream_t s) {
+  if (fax) {  // the stencil alone, then the Fourier factor: the same for both families
+    if constexpr (R == 2) return launch_one<T, 2, 0, true, false>(in, out, N, nb, ncols, tab, fx, s);
+    return cudaErrorInvalidValue;
+  }
+  return leg ? launch_order<T, R, true>(m0, in, out, N, nb, ncols, tab, fx, s)
+             : launch_order<T, R, false>(m0, in, out, N, nb, ncols, tab, fx, s);
 }
 
 template <typename T>
@@ -286,11 +310,14 @@ int build_project_table(sgm_space* s) {
   const int N = (int)s->n[0];
   std::vector<long double> be(N, 0.0L), ga(N, 0.0L);
   for (int j = 0; j < N; ++j) {
-    if (s->kinds[0] == SGM_SHEN_DIRICHLET) {
+    if (s->kinds[0] == SGM_SHEN_DIRICHLET || s->kinds[0] == SGM_LEGENDRE_DIRICHLET) {
       be[j] = -1.0L;
     } else if (s->kinds[0] == SGM_SHEN_BIHARMONIC) {
       be[j] = -2.0L * (j + 2) / (long double)(j + 3);
       ga[j] = (long double)(j + 1) / (long double)(j + 3);
+    } else if (s->kinds[0] == SGM_LEGENDRE_BIHARMONIC) {
+      be[j] = -2.0L * (2 * j + 5) / (long double)(2 * j + 7);
+      ga[j] = (long double)(2 * j + 3) / (long double)(2 * j + 7);
     }
   }
   return s->prec == SGM_F32 ? upload_table<float>(s, be, ga) : upload_table<double>(s, be, ga);
@@ -316,7 +343,9 @@ extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_h
   const int N = s->cheb ? (int)s->n[0] : 1;
   int nb = 1;
   if (s->cheb)
-    nb = s->kinds[0] == SGM_SHEN_DIRICHLET ? N - 2 : s->kinds[0] == SGM_SHEN_BIHARMONIC ? N - 4 : N;
+    nb = (s->kinds[0] == SGM_SHEN_DIRICHLET || s->kinds[0] == SGM_LEGENDRE_DIRICHLET)       ? N - 2
+         : (s->kinds[0] == SGM_SHEN_BIHARMONIC || s->kinds[0] == SGM_LEGENDRE_BIHARMONIC) ? N - 4
+                                                                                           : N;
   const long ncols = s->nspec / N;
   const bool cheb_axis = s->cheb && axis == 0;
   const int m0 = cheb_axis ? order : 0;
@@ -334,11 +363,11 @@ extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_h
   cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e;
   if (s->prec == SGM_F32)
-    e = s->real_spec ? launch_project<float, 1>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
-                     : launch_project<float, 2>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+    e = s->real_spec ? launch_project<float, 1>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<float, 2>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
   else
-    e = s->real_spec ? launch_project<double, 1>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
-                     : launch_project<double, 2>(m0, fax, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+    e = s->real_spec ? launch_project<double, 1>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<double, 2>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
   if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "project_dx: %s", cudaGetErrorString(e));
   return SGM_OK;
 }

@@ -360,6 +360,7 @@ template <typename T>
 int cheb_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide = false) {
   const int N = (int)s->n[0];
   if (sizeof(T) == 4 && s->cheb_tc) return cheb_pass_tc(s, mode, in, out, st, wide);
+  if (s->legendre) return legendre_pass(s, mode, in, out, st, wide);
   long inner = 1;
   for (int i = 1; i < s->ndim; ++i) inner *= s->spec[i];
   FftPlan p = make_plan(N);
@@ -405,6 +406,11 @@ Wavenumbers wavenumbers(const sgm_space* s) {
 
 template <typename T>
 int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void* in, void* out, cudaStream_t st) {
+  // the Legendre kernel takes the biharmonic form a S + (b - 2 a k2) A + (a k2^2 - b k2 + c) B;
+  // a lap(u) + b u is that form with (0, a, b)
+  if (s->legendre)
+    return basis == kDirichlet ? legendre_solve<T>(s, 0.0, a, b, in, out, wavenumbers(s), st)
+                               : legendre_solve<T>(s, a, b, c, in, out, wavenumbers(s), st);
   long ncols = 1;
   for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
   return wrap(launch_solve<T>(basis, s->real_spec, a, b, c, in, out, (int)s->n[0], ncols, wavenumbers(s), s->tab,
@@ -424,9 +430,10 @@ int scalar_impl(sgm_space* s, const void* f, void* out, cudaStream_t st, int mod
 template <typename T> int forward_impl(sgm_space* s, const void* u, void* out, cudaStream_t st) {
   if (!s->cheb) return fourier_forward<T>(s, u, out, st);
   const int basis = s->kinds[0];
-  if (basis == SGM_CHEBYSHEV) return scalar_impl<T>(s, u, out, st, kChebForwardT);
+  if (basis == SGM_CHEBYSHEV || basis == SGM_LEGENDRE) return scalar_impl<T>(s, u, out, st, kChebForwardT);
   SGM_TRY(scalar_impl<T>(s, u, out, st, kChebScalar));
-  if (basis == SGM_SHEN_DIRICHLET) return solve_impl<T>(s, kDirichlet, 0.0, 1.0, 0.0, out, out, st);
+  if (basis == SGM_SHEN_DIRICHLET || basis == SGM_LEGENDRE_DIRICHLET)
+    return solve_impl<T>(s, kDirichlet, 0.0, 1.0, 0.0, out, out, st);
   return solve_impl<T>(s, kBiharmonic, 0.0, 0.0, 1.0, out, out, st);
 }
 
@@ -457,6 +464,9 @@ void free_space(sgm_space* s) {
   cudaFree(s->groups);
   for (void* p : s->tc_img) cudaFree(p);
   cudaFree(s->pdx_tab);
+  for (void* p : s->leg_mat) cudaFree(p);
+  cudaFree(s->leg_band);
+  cudaFree(s->leg_scratch);
   s->magic = 0;
   delete s;
 }
@@ -535,11 +545,16 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (precision != SGM_F32 && precision != SGM_F64) return fail(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
   if (cheb_flags == (SGM_CHEB_TC | SGM_CHEB_AUTO)) return fail(SGM_ERR_ARG, "SGM_CHEB_TC and SGM_CHEB_AUTO exclude each other");
   if (cheb_flags && precision != SGM_F32) return fail(SGM_ERR_ARG, "Chebyshev-axis method flags need an SGM_F32 space");
-  const bool cheb = kinds[0] == SGM_CHEBYSHEV || kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC;
+  auto polynomial = [](int k) {
+    return k == SGM_CHEBYSHEV || k == SGM_SHEN_DIRICHLET || k == SGM_SHEN_BIHARMONIC || k == SGM_LEGENDRE ||
+           k == SGM_LEGENDRE_DIRICHLET || k == SGM_LEGENDRE_BIHARMONIC;
+  };
+  const bool cheb = polynomial(kinds[0]);
+  const bool legendre = kinds[0] == SGM_LEGENDRE || kinds[0] == SGM_LEGENDRE_DIRICHLET || kinds[0] == SGM_LEGENDRE_BIHARMONIC;
   for (int d = 0; d < ndim; ++d) {
     const int k = kinds[d];
-    if (k < SGM_CHEBYSHEV || k > SGM_FOURIER_R2C) return fail(SGM_ERR_ARG, "axis %d: unknown basis kind %d", d, k);
-    if (d > 0 && k <= SGM_SHEN_BIHARMONIC) return fail(SGM_ERR_SIZE, "axis %d: a Chebyshev basis must be axis 0", d);
+    if (k < SGM_CHEBYSHEV || k > SGM_LEGENDRE_BIHARMONIC) return fail(SGM_ERR_ARG, "axis %d: unknown basis kind %d", d, k);
+    if (d > 0 && polynomial(k)) return fail(SGM_ERR_SIZE, "axis %d: a Chebyshev or Legendre basis must be axis 0", d);
     if (k == SGM_FOURIER_R2C && d != ndim - 1) return fail(SGM_ERR_SIZE, "axis %d: only the last axis may be R2C", d);
     if (n[d] < 1 || n[d] > 4096) return fail(SGM_ERR_SIZE, "axis %d: size %lld outside 1..4096", d, (long long)n[d]);
   }
@@ -549,11 +564,16 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] > 2048)
     return fail(SGM_ERR_SIZE, "biharmonic basis needs N <= 2048 (got %lld)", (long long)n[0]);
   if (kinds[0] == SGM_CHEBYSHEV && n[0] < 2) return fail(SGM_ERR_SIZE, "Chebyshev basis needs N >= 2");
+  if (kinds[0] == SGM_LEGENDRE && n[0] < 2) return fail(SGM_ERR_SIZE, "Legendre basis needs N >= 2");
+  if (kinds[0] == SGM_LEGENDRE_DIRICHLET && n[0] < 4) return fail(SGM_ERR_SIZE, "Legendre Dirichlet basis needs N >= 4");
+  if (kinds[0] == SGM_LEGENDRE_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "Legendre biharmonic basis needs N >= 6");
+  // the Legendre transforms are dense N x N matrices held by the space
+  if (legendre && n[0] > 1024) return fail(SGM_ERR_SIZE, "Legendre bases need N <= 1024 (got %lld)", (long long)n[0]);
   if (kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] < 2) return fail(SGM_ERR_SIZE, "R2C axis needs M >= 2");
   if ((cheb_flags & SGM_CHEB_TC) && (!cheb || n[0] > kTcMaxN))
     return fail(SGM_ERR_SIZE, "SGM_CHEB_TC needs a Chebyshev axis of at most %d points", kTcMaxN);
   if (cheb && domain && (domain[0] != -1.0 || domain[1] != 1.0))
-    return fail(SGM_ERR_ARG, "the Chebyshev axis domain must be [-1, 1]");
+    return fail(SGM_ERR_ARG, "the Chebyshev or Legendre axis domain must be [-1, 1]");
   if (domain)
     for (int d = 0; d < ndim; ++d)
       if (!(domain[2 * d + 1] > domain[2 * d])) return fail(SGM_ERR_ARG, "axis %d: empty domain", d);
@@ -569,6 +589,7 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   s->ndim = ndim;
   s->prec = precision;
   s->cheb = cheb;
+  s->legendre = legendre;
   for (int d = 0; d < ndim; ++d) {
     s->kinds[d] = kinds[d];
     s->n[d] = n[d];
@@ -597,7 +618,10 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   chk(cudaMalloc(&s->W1, wbytes), "workspace");
   // W2 holds the spectral intermediate of the physical-to-physical solves, in FP64
   chk(cudaMalloc(&s->W2, (size_t)s->nspec * 16), "workspace");
-  if (st == SGM_OK && cheb) {
+  if (st == SGM_OK && legendre) {
+    st = legendre_build(s, cheb_flags != 0 && n[0] <= kTcMaxN);
+    if (st == SGM_OK) st = build_project_table(s);
+  } else if (st == SGM_OK && cheb) {
     const int N = (int)n[0];
     st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);
     if (st == SGM_OK) st = build_tables(s);
@@ -641,7 +665,9 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   }
   if (st == SGM_OK && cheb && cheb_flags && n[0] <= kTcMaxN) {
     const int N = (int)n[0];
+    // a Legendre space got the images of its dense matrices from legendre_build
     for (int mode : {kChebScalar, kChebBackward, kChebForwardT}) {
+      if (legendre) continue;
       const std::vector<uint16_t> img = tc_cheb_image(mode, kinds[0], N);
       chk(cudaMalloc(&s->tc_img[mode], img.size() * 2), "contraction matrix");
       if (st == SGM_OK)
@@ -710,11 +736,16 @@ int sgm_backward(sgm_space* s, const void* u_hat, void* u, void* stream) {
   return s->prec == SGM_F32 ? backward_impl<float>(s, u_hat, u, st) : backward_impl<double>(s, u_hat, u, st);
 }
 
+// the Helmholtz solver needs a Dirichlet basis, the biharmonic solver a biharmonic one (either family)
+static bool solver_matches(const sgm_space* s, int basis) {
+  const int k = s->kinds[0];
+  if (basis == kDirichlet) return k == SGM_SHEN_DIRICHLET || k == SGM_LEGENDRE_DIRICHLET;
+  return k == SGM_SHEN_BIHARMONIC || k == SGM_LEGENDRE_BIHARMONIC;
+}
+
 static int solve_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u, void* stream) {
   SGM_TRY(check_space(s));
-  if ((basis == kDirichlet && s->kinds[0] != SGM_SHEN_DIRICHLET) ||
-      (basis == kBiharmonic && s->kinds[0] != SGM_SHEN_BIHARMONIC))
-    return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
+  if (!solver_matches(s, basis)) return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
   if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
     return fail(SGM_ERR_ARG, "coefficients must be finite");
   if (basis == kDirichlet && a == 0.0 && b == 0.0) return fail(SGM_ERR_ARG, "a = b = 0 gives a singular system");
@@ -740,9 +771,7 @@ int sgm_biharmonic_solve(sgm_space* s, double a, double b, double c, const void*
 // Chebyshev kernels widen/narrow the intermediate.
 static int full_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u, void* stream) {
   SGM_TRY(check_space(s));
-  if ((basis == kDirichlet && s->kinds[0] != SGM_SHEN_DIRICHLET) ||
-      (basis == kBiharmonic && s->kinds[0] != SGM_SHEN_BIHARMONIC))
-    return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
+  if (!solver_matches(s, basis)) return fail(SGM_ERR_STATE, "axis 0 basis does not match this solver");
   if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(c))
     return fail(SGM_ERR_ARG, "coefficients must be finite");
   if (basis == kDirichlet && a == 0.0 && b == 0.0) return fail(SGM_ERR_ARG, "a = b = 0 gives a singular system");

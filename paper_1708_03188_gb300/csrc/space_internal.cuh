@@ -16,7 +16,8 @@ struct sgm_space {
   int64_t n[3] = {1, 1, 1};
   double dom[6] = {0, 0, 0, 0, 0, 0};
   int prec = SGM_F64;
-  bool cheb = false;       // axis 0 is a Chebyshev axis
+  bool cheb = false;       // axis 0 is a polynomial axis (Chebyshev or Legendre family)
+  bool legendre = false;   // axis 0 is a Legendre basis (legendre.cu)
   bool real_phys = false;  // physical array is real
   bool real_spec = false;  // spectral array is real (1-D Chebyshev)
   int64_t spec[3] = {1, 1, 1};
@@ -36,6 +37,10 @@ struct sgm_space {
   int cheb_tc = 0;           // 1: Chebyshev axis by the tensor-core contraction (k_cheb_tc.cu)
   void* tc_img[3] = {nullptr, nullptr, nullptr};  // contraction matrices per ChebMode
   void* pdx_tab = nullptr;   // Shen-to-Chebyshev stencil coefficients of sgm_project_dx (project.cu)
+  void* leg_mat[3] = {nullptr, nullptr, nullptr};  // Legendre axis-0 matrices per ChebMode (legendre.cu)
+  double* leg_band = nullptr;   // band entries of the Legendre Galerkin matrices, 6 per basis row
+  double* leg_scratch = nullptr;
+  long leg_threads = 0;
 
   size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
   size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
@@ -51,4 +56,15 @@ int make_fast_twiddles(int precision, int L, void** out);
 // stencil coefficient table of sgm_project_dx for a space with a Chebyshev axis (project.cu);
 // stored in s->pdx_tab, freed with the space
 int build_project_table(sgm_space* s);
+// Legendre axis 0 (legendre.cu): tables, matrices and solve scratch of a new space, plus the
+// tensor-core images of its matrices in s->tc_img when tc_images (FP32, N <= 128; all freed with
+// the space); one axis-0 pass (mode: ChebMode; wide: the spectral side is FP64 on an FP32 space);
+// the banded FP64 solve of a (S - 2 k2 A + k2^2 B) + b (A - k2 B) + c B, the biharmonic weak form
+// (a Dirichlet problem a lap(u) + b u = f is (0, a, b): its tables have S = 0), on spectral data
+// of type TS (float or double)
+int legendre_build(sgm_space* s, bool tc_images);
+int legendre_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide);
+template <typename TS>
+int legendre_solve(sgm_space* s, double a, double b, double c, const void* in, void* out, const Wavenumbers& wn,
+                   cudaStream_t st);
 }  // namespace sgm

@@ -13,7 +13,9 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgm.so")
 
-KINDS = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2, "c2c": 3, "r2c": 4}
+KINDS = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2, "c2c": 3, "r2c": 4,
+         "legendre": 5, "legendre_dirichlet": 6, "legendre_biharmonic": 7}
+POLYNOMIAL = ("chebyshev", "dirichlet", "biharmonic", "legendre", "legendre_dirichlet", "legendre_biharmonic")
 PRECISION = {"f32": 1, "f64": 2}
 CHEB_METHOD = {"fft": 0, "tc": 0x10, "auto": 0x20}
 _VP = ctypes.c_void_p
@@ -102,7 +104,7 @@ def _ptr(t):
 
 
 class Space:
-    """Tensor-product space (one Chebyshev axis 0 + Fourier axes, or Fourier axes only).
+    """Tensor-product space (one Chebyshev or Legendre axis 0 + Fourier axes, or Fourier axes only).
 
     kinds: names from KINDS; sizes: quadrature points per axis; domain: [(lo, hi)] per
     axis or None; precision "f32" (FP32 transforms, FP64 solves) or "f64"; cheb (f32 only):
@@ -127,7 +129,7 @@ class Space:
                                      PRECISION[precision] | CHEB_METHOD[cheb]))
         self.physical_shape = self._shape(0)
         self.spectral_shape = self._shape(1)
-        cheb = self.kinds[0] in ("chebyshev", "dirichlet", "biharmonic")
+        cheb = self.kinds[0] in POLYNOMIAL
         self.real_physical = self.kinds[-1] == "r2c" or (cheb and nd == 1)
         self.real_spectral = cheb and nd == 1
         rdt = torch.float32 if precision == "f32" else torch.float64
@@ -142,10 +144,13 @@ class Space:
 
     @property
     def cheb_method(self):
-        """"tc" if the Chebyshev axis runs as the tensor-core contraction, else "fft"."""
+        """"tc" if axis 0 runs as the tensor-core contraction, else "fft" (Chebyshev: DCT via FFT)
+        or "dense" (Legendre: the dense CUDA-core product)."""
         m = ctypes.c_int()
         check(lib().sgm_space_cheb_method(self._h, ctypes.byref(m)))
-        return "tc" if m.value else "fft"
+        if m.value:
+            return "tc"
+        return "dense" if self.kinds[0].startswith("legendre") else "fft"
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
@@ -223,11 +228,14 @@ class Space:
         return out
 
     def chebyshev_space(self):
-        """W0: this space with axis 0 replaced by the regular Chebyshev basis (a new Space with
-        the same sizes, domain and precision); for a Fourier-only space, a copy of it."""
+        """W0: this space with axis 0 replaced by the regular basis of its family, Chebyshev or
+        Legendre (a new Space with the same sizes, domain and precision); for a Fourier-only
+        space, a copy of it."""
         kinds = list(self.kinds)
         if kinds[0] in ("dirichlet", "biharmonic"):
             kinds[0] = "chebyshev"
+        elif kinds[0] in ("legendre_dirichlet", "legendre_biharmonic"):
+            kinds[0] = "legendre"
         return Space(kinds, self.sizes, domain=self.domain, precision=self.precision)
 
 

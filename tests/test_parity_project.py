@@ -64,6 +64,10 @@ SPACES = [
     (["dirichlet", "c2c", "r2c"], [24, 10, 18], None),
     (["biharmonic", "c2c", "r2c"], [40, 6, 301], None),  # 906 columns: 8 CTAs, the last one ragged
     (["dirichlet", "c2c"], [16, 12], [(-1.0, 1.0), (0.0, 7.0)]),
+    (["legendre"], [9], None),                        # Legendre bases: W0 is the regular Legendre basis
+    (["legendre_dirichlet"], [41], None),
+    (["legendre_biharmonic", "r2c"], [13, 6], None),
+    (["legendre_biharmonic", "c2c", "r2c"], [40, 6, 301], None),
     (["c2c", "r2c"], [12, 16], None),                 # Fourier-only spaces: one row, W0 = the space
     (["c2c"], [30], None),
     (["c2c", "c2c"], [16, 16], [(-50.0, 50.0), (-50.0, 50.0)]),
