@@ -360,12 +360,21 @@ int sgm_unpack_add(const float* d, void* u, int B, int H, int W, float scale, vo
  *   ndim, kinds, n, domain, precision   as for sgm_space_create; kinds[0] must be
  *                                       SGM_SHEN_DIRICHLET and 4 <= n[0] <= 2048.
  *   a, b, f_tilde, u_hat, stream        as for sgm_helmholtz_solve (in place allowed).
- * Scratch: an 8 MiB array in the library's device memory, reserved on every GPU that loads
- * the library and held until the process exits.  The first call on each device looks up
- * the array's device address (with that device current); make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's contents
- * (nothing in it needs to start at zero); calls whose kernels overlap on the GPU, e.g. on
- * two streams, race on it, so serialise them.  Sizes past the limit return SGM_ERR_SIZE.
+ *   domain may be NULL; when given, axis 0 must be [-1, 1].
+ * Scratch: an 8 MiB array in the library's device memory, held until the process exits.
+ * With CUDA's lazy module loading it is reserved on a device by the first call there, which
+ * also looks up the array's device address (with that device current) and caches it.  Make
+ * that first call before any stream capture, and before a fixed-budget caller claims the rest
+ * of the device's memory (otherwise the first call can fail with SGM_ERR_CUDA).  The cached
+ * address belongs to the primary context: do not call this entry point again after
+ * cudaDeviceReset in the same process.  All calls share the array and it keeps the last
+ * call's contents (nothing in it needs to start at zero); calls whose kernels overlap on the
+ * GPU, e.g. on two streams, race on it, so serialise them.  Sizes past the limit return
+ * SGM_ERR_SIZE.
+ * Cost: the array bounds the number of threads to 8 MiB / (32 B (N/2 + 1)), i.e. 128-thread
+ * CTAs: 15 at N = 256, 3 at N = 1024, 2 from N = 1364 and 1 at N = 2048, against one thread per
+ * (column, parity) for sgm_helmholtz_solve.  Large N on many columns therefore runs on few SMs;
+ * use this entry point where allocation is impossible, not for throughput at large N.
  */
 int sgm_helmholtz_solve_noalloc(int ndim, const int* kinds, const int64_t* n, const double* domain,
                                 int precision, double a, double b, const void* f_tilde, void* u_hat,

@@ -9,14 +9,17 @@
 // space API for this step.
 //
 // How: the elimination scratch of k_solve_dirichlet (one FP64 record per row per thread)
-// lives in a file-scope __device__ array of fixed size (kStaticScratchBytes), created with
-// the module and held by every GPU that loads the library until the process exits.  The
+// lives in a file-scope __device__ array of fixed size (kStaticScratchBytes).  Under CUDA's
+// lazy module loading the array is reserved on a device when this module is first used there
+// (the first call's address lookup), and it is then held until the process exits.  The
 // Galerkin coefficients are evaluated inline from their closed forms instead of being
 // read from a table, so no other device memory is needed.  Host code cannot use the
 // array's name as a device address: on the first call on each device (with that device
 // current) the entry point looks its address up with cudaGetSymbolAddress, checks the
 // result and caches it per device; that first call must therefore come before any stream
-// capture.  Calls reuse the same array and it keeps the last call's contents; nothing in it
+// capture, and before a caller with a fixed memory budget claims the rest of the device.
+// The cached address belongs to the device's primary context: after cudaDeviceReset the
+// library must be reloaded before this entry point is called again.  Calls reuse the same array and it keeps the last call's contents; nothing in it
 // needs clearing, because every value a thread reads back was written earlier by the same
 // thread in the same call.  Calls whose kernels overlap on the GPU (for example on two
 // streams) race on the array and must be serialised by the caller.
@@ -163,11 +166,14 @@ extern "C" int sgm_helmholtz_solve_noalloc(int ndim, const int* kinds, const int
   if (n[0] < 4 || n[0] > kNoallocMaxN)
     return set_error(SGM_ERR_SIZE, "N = %lld outside 4..%d, the largest size whose elimination scratch fits the "
                      "%zu-byte static array", (long long)n[0], kNoallocMaxN, kStaticScratchBytes);
+  if (domain && (domain[0] != -1.0 || domain[1] != 1.0))
+    return set_error(SGM_ERR_ARG, "the Chebyshev axis is defined on [-1, 1] only");
   for (int d = 1; d < ndim; ++d) {
     if (kinds[d] != SGM_FOURIER_C2C && kinds[d] != SGM_FOURIER_R2C)
       return set_error(SGM_ERR_SIZE, "axis %d must be a Fourier axis", d);
     if (kinds[d] == SGM_FOURIER_R2C && d != ndim - 1) return set_error(SGM_ERR_SIZE, "only the last axis may be R2C");
     if (n[d] < 1 || n[d] > 4096) return set_error(SGM_ERR_SIZE, "axis %d: size outside 1..4096", d);
+    if (kinds[d] == SGM_FOURIER_R2C && n[d] < 2) return set_error(SGM_ERR_SIZE, "R2C axis needs M >= 2");
     if (domain && !(domain[2 * d + 1] > domain[2 * d])) return set_error(SGM_ERR_ARG, "axis %d: empty domain", d);
   }
   if (!std::isfinite(a) || !std::isfinite(b)) return set_error(SGM_ERR_ARG, "coefficients must be finite");

@@ -70,3 +70,21 @@ def test_mse_gradient_finite_difference():
         o[i] -= 2 * h
         lm, _ = cnn.mse(o, tgt)
         assert abs((lp - lm) / (2 * h) - grad[i]) < 1e-8
+
+
+def test_adamw_constant_gradient_closed_form_over_many_steps():
+    # With a constant gradient g and zero initial moments, m_t = (1 - beta1^t) g and
+    # v_t = (1 - beta2^t) g^2 exactly, so the bias-corrected ratio is g / |g| at every step t
+    # and each update is lr * (sign(g) + wd * w) up to eps.  A bias correction that drops the
+    # exponent (beta instead of beta^t) passes step 1 but fails from step 2 on.
+    g = np.array([3.0, -0.5, 1e-3, -7.0])
+    w = np.array([1.0, 2.0, -1.0, 0.25])
+    m, v = np.zeros(4), np.zeros(4)
+    lr, b1, b2, wd = 0.05, 0.9, 0.999, 0.01
+    expect = w.copy()
+    for t in range(1, 8):
+        w, m, v = cnn.adamw_step(w, g, m, v, t, lr, b1, b2, 1e-14, wd)
+        expect = expect - lr * (np.sign(g) + wd * expect)
+        assert np.allclose(m, (1 - b1 ** t) * g, rtol=1e-14, atol=0)
+        assert np.allclose(v, (1 - b2 ** t) * g * g, rtol=1e-13, atol=0)
+        assert np.allclose(w, expect, rtol=0, atol=1e-9), t
