@@ -348,6 +348,16 @@ int sgm_pack_channels(const void* u, void* x, int B, int H, int W, float scale, 
 int sgm_unpack_add(const float* d, void* u, int B, int H, int W, float scale, void* stream);
 
 /*
+ * Fused multiply-add throughput probe (a measurement utility, no counterpart in the paper).
+ * Launches blocks x threads threads, each running 8 independent FMA chains for `iters`
+ * rounds in FP64 (precision SGM_F64) or FP32 (SGM_F32), and writes one value per thread to
+ * the device array `sink` (blocks * threads doubles or floats).  *flops (host) receives the
+ * flop count of the launch (2 per FMA), to be divided by the launch's event-timed duration.
+ * threads: a multiple of 32 in 32..256; SGM_ERR_SIZE otherwise.
+ */
+int sgm_alu_probe(int precision, int blocks, int threads, int64_t iters, void* sink, double* flops, void* stream);
+
+/*
  * Dirichlet Helmholtz solve that allocates nothing (no counterpart in the paper; it is an
  * interface choice of this library).
  *

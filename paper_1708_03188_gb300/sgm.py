@@ -60,6 +60,8 @@ _SIGNATURES = {
     "sgm_spectral_truncate": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     "sgm_pack_channels": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
     "sgm_unpack_add": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
+    "sgm_alu_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _VP,
+                                     ctypes.POINTER(_D), _VP]),
     "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                    ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_D), ctypes.c_int,
                                                    _D, _D, _VP, _VP, _VP]),
@@ -433,3 +435,15 @@ def tc_wait_timeouts(reset=False):
     c = ctypes.c_int()
     check(lib().sgm_tc_wait_timeouts(ctypes.byref(c), 1 if reset else 0))
     return c.value
+
+
+def alu_probe(precision, blocks, threads, iters, sink, stream=None):
+    """Launch the FMA throughput probe (sgm_alu_probe) and return its flop count; `sink` is a
+    float32/float64 CUDA tensor of at least blocks * threads elements."""
+    want = torch.float64 if precision == "f64" else torch.float32
+    if not sink.is_cuda or sink.dtype != want or sink.numel() < blocks * threads:
+        raise ValueError(f"sink: CUDA {want} tensor of >= {blocks * threads} elements")
+    fl = _D()
+    check(lib().sgm_alu_probe(PRECISION[precision], blocks, threads, iters, _ptr(sink), ctypes.byref(fl),
+                              _stream(stream)))
+    return fl.value

@@ -12,7 +12,7 @@
 - Backward transform of a full random spectrum (complex N(0,1) exp(-|k|/16) on the basis rows,
   Hermitian on the two self-conjugate R2C planes) on sampled output rows u(x_j, y_i, :): the
   oracle's basis values summed over k, a dense inverse DFT over l1 and the Hermitian sum over l2.
-  FP32 1e-5 and FP64 1e-12 relative per row.
+  FP32 1e-5 and FP64 1e-12 per row, relative to the field's root-mean-square row.
 - The fused physical-to-physical path the bench times (sgm_helmholtz / sgm_biharmonic, FP64
   spectral intermediate) on a right-hand side with 24 Fourier modes of white-noise x-profiles,
   over the whole box: the oracle solves each mode's column (quadrature scalar product, dense
@@ -147,9 +147,13 @@ def test_backward_random_spectrum_sampled_rows(kind, prec, tol):
     u = sp.backward(torch.from_numpy(c).to(sp.spectral_dtype).cuda()).cpu().numpy().astype(np.float64)
     g = inputs.rng("box3d", 730)
     rows = [(0, 0), (N - 1, N - 1), (N // 2, 1)] + list(zip(g.integers(0, N, 13).tolist(), g.integers(0, N, 13).tolist()))
+    # Error of a row relative to the root-mean-square row of the field: near x = +-1 the basis
+    # functions vanish (to second order for the biharmonic basis), so a row there is small
+    # while the transform's rounding is set by the whole spectrum.
+    scale = np.linalg.norm(u) / np.sqrt(u.shape[0] * u.shape[1])
     worst = 0.0
     for j, i in rows:
-        e = rel(u[j, i], oracle_row(kind, c, j, i))
+        e = np.linalg.norm(u[j, i] - oracle_row(kind, c, j, i)) / scale
         worst = max(worst, e)
         assert e < tol, (j, i, e)
     print(f"{kind} {prec} backward, {len(rows)} sampled rows: worst {worst:.2e}")
