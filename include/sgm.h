@@ -224,6 +224,25 @@ int sgm_biharmonic(sgm_space* space, double a, double b, double c, const void* f
 int sgm_project_dx(sgm_space* space, int axis, int order, const void* u_hat, void* du_hat,
                    void* stream);
 
+/*
+ * Projection onto another space, project(Dx(u, axis, order), W) of Sec. 5 with any target W
+ * that differs from this space at most in the basis of axis 0: the regular basis of the same
+ * family (then identical to sgm_project_dx) or a Shen basis of that family (SGM_SHEN_DIRICHLET,
+ * SGM_SHEN_BIHARMONIC, or the Legendre ones).  For a Shen target the result is the Galerkin
+ * projection: the coefficients c in W with (sum_j c_j psi_j, psi_k)_w = (d^m u, psi_k)_w for every
+ * basis function psi_k of W, computed from the derivative's regular coefficients d (as
+ * sgm_project_dx) by the exact scalar products S_k = w_k d_k + beta_k w_{k+2} d_{k+2} + gamma_k
+ * w_{k+4} d_{k+4} (w_k = pi c_k / 2 Chebyshev, 2 / (2k+1) Legendre; beta, gamma the target's
+ * stencil) and the FP64 mass solve of the forward transform (Sec. 3.4.2).
+ *   target   a live space of the same ndim, sizes, domains and precision (SGM_ERR_STATE
+ *            otherwise); Fourier-only spaces: target has the same kinds.
+ *   u_hat    spectral array of `space`; out_hat: spectral array of `target` (all N rows
+ *            written, rows past the target basis zero).  Out of place (SGM_ERR_ALIAS).
+ * Uses the workspaces of both spaces: calls on either space must not overlap on the GPU.
+ */
+int sgm_project(sgm_space* space, int axis, int order, const void* u_hat, sgm_space* target, void* out_hat,
+                void* stream);
+
 /* ---- complex Ginzburg-Landau equation (Sec. 6 of the paper) ------------------------------- */
 #define SGM_GL_RK4 0      /* explicit classical RK4, the paper's time loop */
 #define SGM_GL_IFRK4 1    /* classical RK4 on exp(-L t) u_hat (linear part integrated exactly) */

@@ -145,21 +145,24 @@ class Space:
                                       lambda k2: galerkin.biharmonic_matrix(mats, a, b, c, k2))
 
     # ---- derivatives (Sec. 5) ------------------------------------------------------------
-    def project_dx(self, u_hat, axis, order):
+    def project_dx(self, u_hat, axis, order, target=None):
         """project(Dx(u, axis, order), W0) of Sec. 5 for the Function with coefficients u_hat.
 
-        W0 is this space with axis 0 replaced by the regular basis of its family, T_k or L_k
-        (W0 is the space itself when every axis is a Fourier axis).  The projection onto W0 is the forward
-        transform of Sec. 3.4.2 applied to the derivative, written with Galerkin matrices:
-          Chebyshev axis    B0^{-1} C u_hat, with C[k, l] = (d^m phi_l / dx^m, T_k)_w^N and the
-                            regular basis' mass matrix B0[k, j] = (T_j, T_k)_w^N, both by
-                            Gauss-Chebyshev quadrature (the projection of the basis functions
-                            alone, m = 0, when the derivative is along a Fourier axis);
+        W0 is this space with axis 0 replaced by `target` (default: the regular basis of its
+        family, T_k or L_k; a Shen basis of the same family may be named instead, e.g.
+        "dirichlet" or "biharmonic"); W0 is the space itself when every axis is a Fourier axis.
+        The projection onto W0 is the forward transform of Sec. 3.4.2 applied to the
+        derivative, written with Galerkin matrices:
+          Chebyshev axis    B0^{-1} C u_hat, with C[k, l] = (d^m phi_l / dx^m, psi_k)_w^N and
+                            W0's mass matrix B0[k, j] = (psi_j, psi_k)_w^N (psi the basis of
+                            W0 along axis 0), both by Gauss quadrature (the projection of the
+                            basis functions alone, m = 0, when the derivative is along a
+                            Fourier axis);
           Fourier axis d    the Fourier inner products of Sec. 3.4.1 give the factor
                             (i k)^m, k = 2 pi l / L_d with the stored wavenumber l (FFT order;
                             an R2C axis keeps l = 0..M/2).
         Rows of u_hat past the basis size are ignored.  Returns the coefficients in W0's
-        spectral layout (all N rows along axis 0).
+        spectral layout (all N rows along axis 0, rows past W0's basis size zero).
         """
         u_hat = np.asarray(u_hat)
         ndim = len(self.kinds)
@@ -168,14 +171,18 @@ class Space:
         if self.has_cheb:
             kind, N = self.kinds[0], self.sizes[0]
             m0 = order if axis == 0 else 0
+            tk = quadrature.regular_kind(kind) if target is None else target
+            assert quadrature.family(tk) == quadrature.family(kind), "target must be of the same family"
             x, w = quadrature.points(kind, N)
-            T = quadrature.basis_values(quadrature.regular_kind(kind), N, x)   # T_k (or L_k) at x_j
+            T = quadrature.basis_values(tk, N, x)                 # psi_k at x_j, (N, nt)
             V = quadrature.basis_values(kind, N, x, deriv=m0)     # phi_l^(m0)(x_j), (N, nb)
-            nb = V.shape[1]
+            nb, nt = V.shape[1], T.shape[1]
             Tw = T * w[:, None]
             C = Tw.T @ V
             B0 = Tw.T @ T
-            out = np.tensordot(np.linalg.solve(B0, C), out[:nb], axes=([1], [0]))
+            res = np.tensordot(np.linalg.solve(B0, C), out[:nb], axes=([1], [0]))
+            out = np.zeros((N,) + res.shape[1:], dtype=res.dtype)
+            out[:nt] = res
         if not (self.has_cheb and axis == 0):
             M = self.sizes[axis]
             L = self.domains[axis][1] - self.domains[axis][0]

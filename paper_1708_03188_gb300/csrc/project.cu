@@ -33,10 +33,17 @@
 // errors summed in lo without renormalising (the cascaded sums of Ogita, Rump and Oishi 2005,
 // "Accurate sum and dot product").  The result is as accurate as a computation in about twice
 // FP32 precision rounded once, and the FP64 pipe (1/64 of the FP32 rate on this GPU) stays idle.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
 #include "space_internal.cuh"
+
+#define PROJECT_TRY(expr)        \
+  do {                           \
+    const int _st = (expr);      \
+    if (_st != SGM_OK) return _st; \
+  } while (0)
 
 namespace sgm {
 namespace {
@@ -303,6 +310,68 @@ int upload_table(sgm_space* s, const std::vector<long double>& be, const std::ve
   return SGM_OK;
 }
 
+// Projection onto a Shen space W (Sec. 5, project with a composite target basis).  Given the
+// regular coefficients d (T_k or L_k) of a function, its Galerkin projection onto W has the
+// scalar products S_k = (sum_j d_j T_j, psi_k)_w, and (T_j, T_k)_w = w_k delta_jk with
+// w_k = pi c_k / 2 (Chebyshev, c_0 = 2) or 2 / (2k + 1) (Legendre), so for
+// psi_k = T_k + beta_k T_{k+2} + gamma_k T_{k+4}
+//   S_k = w_k d_k + beta_k w_{k+2} d_{k+2} + gamma_k w_{k+4} d_{k+4},   k < nt (rows past: 0),
+// exact, since Gauss quadrature with N points integrates these degree < 2N - 1 products
+// exactly.  The coefficients follow from the mass solve B c = S (space_mass_solve_f64).  S is
+// formed in FP64 from the (FP32 or FP64) d, one thread per (row, column) with consecutive
+// threads on consecutive columns.
+struct ShenStencil {
+  int legendre;    // 1: Legendre weights 2/(2k+1)
+  int kind;        // kDirichlet or kBiharmonic (target basis)
+};
+
+__device__ __forceinline__ double series_weight(int legendre, int k) {
+  if (legendre) return 2.0 / (2.0 * k + 1.0);
+  return k == 0 ? 3.141592653589793 : 1.5707963267948966;
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(256) k_shen_scalar_of_series(const T* __restrict__ d, double* __restrict__ S, int N,
+                                                              int nt, long ncols, ShenStencil st) {
+  const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (long)N * ncols) return;
+  const int k = (int)(idx / ncols);
+  const long c = idx - (long)k * ncols;
+  double out[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) out[r] = 0.0;
+  if (k < nt) {
+    double be, ga = 0.0;
+    if (st.kind == kDirichlet) {
+      be = -1.0;
+    } else if (st.legendre) {
+      be = -2.0 * (2 * k + 5) / (double)(2 * k + 7);
+      ga = (double)(2 * k + 3) / (double)(2 * k + 7);
+    } else {
+      be = -2.0 * (k + 2) / (double)(k + 3);
+      ga = (double)(k + 1) / (double)(k + 3);
+    }
+    const double w0 = series_weight(st.legendre, k), w2 = be * series_weight(st.legendre, k + 2),
+                 w4 = ga * series_weight(st.legendre, k + 4);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const double a0 = (double)d[((long)k * ncols + c) * R + r];
+      const double a2 = k + 2 < N ? (double)d[((long)(k + 2) * ncols + c) * R + r] : 0.0;
+      const double a4 = k + 4 < N ? (double)d[((long)(k + 4) * ncols + c) * R + r] : 0.0;
+      out[r] = fma(w4, a4, fma(w2, a2, w0 * a0));
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) S[idx * R + r] = out[r];
+}
+
+// FP64 -> T, n values (round to nearest)
+template <typename T>
+__global__ void __launch_bounds__(256) k_narrow_copy(const double* __restrict__ in, T* __restrict__ out, long n) {
+  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = (T)in[i];
+}
+
 }  // namespace
 
 int build_project_table(sgm_space* s) {
@@ -327,19 +396,11 @@ int build_project_table(sgm_space* s) {
 
 using namespace sgm;
 
-extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_hat, void* du_hat, void* stream) {
-  const int st = space_check(s);
-  if (st != SGM_OK) return st;
-  if (axis < 0 || axis >= s->ndim) return set_error(SGM_ERR_ARG, "axis %d outside 0..%d", axis, s->ndim - 1);
-  if (order < 0 || order > kMaxOrder) return set_error(SGM_ERR_ARG, "order %d outside 0..%d", order, kMaxOrder);
-  if (!u_hat || !du_hat) return set_error(SGM_ERR_NULL, "NULL data pointer");
-  if (((uintptr_t)u_hat & 15) || ((uintptr_t)du_hat & 15))
-    return set_error(SGM_ERR_ALIGN, "data pointers must be 16-byte aligned");
-  const char* a = (const char*)u_hat;
-  const char* b = (const char*)du_hat;
-  if (a < b + s->spec_bytes && b < a + s->spec_bytes) return set_error(SGM_ERR_ALIAS, "u_hat and du_hat overlap");
-  if (s->cheb && !s->pdx_tab) return set_error(SGM_ERR_STATE, "space has no derivative stencil table");
+namespace {
 
+// project(Dx(u, axis, order), W0) with W0 the regular basis: writes the regular coefficients to
+// `out` (spectral layout of s, type of s's precision).  Arguments checked by the callers.
+int project_regular(sgm_space* s, int axis, int order, const void* u_hat, void* out, cudaStream_t cs) {
   const int N = s->cheb ? (int)s->n[0] : 1;
   int nb = 1;
   if (s->cheb)
@@ -360,14 +421,98 @@ extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_h
     fx.order = order;
     fx.scale = 2.0 * 3.14159265358979323846 / (s->dom[2 * axis + 1] - s->dom[2 * axis]);
   }
-  cudaStream_t cs = (cudaStream_t)stream;
   cudaError_t e;
   if (s->prec == SGM_F32)
-    e = s->real_spec ? launch_project<float, 1>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
-                     : launch_project<float, 2>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+    e = s->real_spec ? launch_project<float, 1>(m0, fax, s->legendre, u_hat, out, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<float, 2>(m0, fax, s->legendre, u_hat, out, N, nb, ncols, s->pdx_tab, fx, cs);
   else
-    e = s->real_spec ? launch_project<double, 1>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs)
-                     : launch_project<double, 2>(m0, fax, s->legendre, u_hat, du_hat, N, nb, ncols, s->pdx_tab, fx, cs);
+    e = s->real_spec ? launch_project<double, 1>(m0, fax, s->legendre, u_hat, out, N, nb, ncols, s->pdx_tab, fx, cs)
+                     : launch_project<double, 2>(m0, fax, s->legendre, u_hat, out, N, nb, ncols, s->pdx_tab, fx, cs);
   if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "project_dx: %s", cudaGetErrorString(e));
+  return SGM_OK;
+}
+
+int project_args(sgm_space* s, int axis, int order, const void* u_hat, const void* du_hat) {
+  const int st = space_check(s);
+  if (st != SGM_OK) return st;
+  if (axis < 0 || axis >= s->ndim) return set_error(SGM_ERR_ARG, "axis %d outside 0..%d", axis, s->ndim - 1);
+  if (order < 0 || order > kMaxOrder) return set_error(SGM_ERR_ARG, "order %d outside 0..%d", order, kMaxOrder);
+  if (!u_hat || !du_hat) return set_error(SGM_ERR_NULL, "NULL data pointer");
+  if (((uintptr_t)u_hat & 15) || ((uintptr_t)du_hat & 15))
+    return set_error(SGM_ERR_ALIGN, "data pointers must be 16-byte aligned");
+  const char* a = (const char*)u_hat;
+  const char* b = (const char*)du_hat;
+  if (a < b + s->spec_bytes && b < a + s->spec_bytes) return set_error(SGM_ERR_ALIAS, "u_hat and du_hat overlap");
+  if (s->cheb && !s->pdx_tab) return set_error(SGM_ERR_STATE, "space has no derivative stencil table");
+  return SGM_OK;
+}
+
+bool is_regular(int kind) { return kind == SGM_CHEBYSHEV || kind == SGM_LEGENDRE; }
+bool is_legendre_kind(int kind) {
+  return kind == SGM_LEGENDRE || kind == SGM_LEGENDRE_DIRICHLET || kind == SGM_LEGENDRE_BIHARMONIC;
+}
+
+}  // namespace
+
+extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_hat, void* du_hat, void* stream) {
+  const int st = project_args(s, axis, order, u_hat, du_hat);
+  if (st != SGM_OK) return st;
+  return project_regular(s, axis, order, u_hat, du_hat, (cudaStream_t)stream);
+}
+
+extern "C" int sgm_project(sgm_space* s, int axis, int order, const void* u_hat, sgm_space* target, void* out_hat,
+                           void* stream) {
+  int st = project_args(s, axis, order, u_hat, out_hat);
+  if (st != SGM_OK) return st;
+  st = space_check(target);
+  if (st != SGM_OK) return st;
+  if (target->ndim != s->ndim || target->prec != s->prec || target->cheb != s->cheb)
+    return set_error(SGM_ERR_STATE, "target space differs in dimension, precision or axis-0 family");
+  for (int d = 0; d < s->ndim; ++d) {
+    if (target->n[d] != s->n[d] || target->dom[2 * d] != s->dom[2 * d] || target->dom[2 * d + 1] != s->dom[2 * d + 1])
+      return set_error(SGM_ERR_STATE, "target space differs in size or domain along axis %d", d);
+    if (d > 0 || !s->cheb)
+      if (target->kinds[d] != s->kinds[d]) return set_error(SGM_ERR_STATE, "target space differs along Fourier axis %d", d);
+  }
+  const char* a = (const char*)u_hat;
+  const char* b = (const char*)out_hat;
+  if (a < b + target->spec_bytes && b < a + target->spec_bytes) return set_error(SGM_ERR_ALIAS, "u_hat and out_hat overlap");
+  cudaStream_t cs = (cudaStream_t)stream;
+  if (!s->cheb || is_regular(target->kinds[0])) {
+    if (s->cheb && is_legendre_kind(target->kinds[0]) != (bool)s->legendre)
+      return set_error(SGM_ERR_STATE, "target basis is of another polynomial family");
+    return project_regular(s, axis, order, u_hat, out_hat, cs);
+  }
+  if (is_legendre_kind(target->kinds[0]) != (bool)s->legendre)
+    return set_error(SGM_ERR_STATE, "target basis is of another polynomial family");
+  // regular coefficients of the derivative in s->W1, the target's scalar products in FP64 in
+  // target->W2, the FP64 mass solve in place, then the result in the space's precision
+  PROJECT_TRY(project_regular(s, axis, order, u_hat, s->W1, cs));
+  const int N = (int)s->n[0];
+  const long ncols = s->nspec / N;
+  const int tk = target->kinds[0];
+  ShenStencil sst{target->legendre ? 1 : 0,
+                  (tk == SGM_SHEN_DIRICHLET || tk == SGM_LEGENDRE_DIRICHLET) ? (int)kDirichlet : (int)kBiharmonic};
+  const int nt = sst.kind == kDirichlet ? N - 2 : N - 4;
+  const long total = (long)N * ncols;
+  const unsigned grid = (unsigned)((total + 255) / 256);
+  const int R = s->real_spec ? 1 : 2;
+  void* S = (s->prec == SGM_F64) ? out_hat : target->W2;
+  if (s->prec == SGM_F32) {
+    if (R == 1) k_shen_scalar_of_series<float, 1><<<grid, 256, 0, cs>>>((const float*)s->W1, (double*)S, N, nt, ncols, sst);
+    else k_shen_scalar_of_series<float, 2><<<grid, 256, 0, cs>>>((const float*)s->W1, (double*)S, N, nt, ncols, sst);
+  } else {
+    if (R == 1) k_shen_scalar_of_series<double, 1><<<grid, 256, 0, cs>>>((const double*)s->W1, (double*)S, N, nt, ncols, sst);
+    else k_shen_scalar_of_series<double, 2><<<grid, 256, 0, cs>>>((const double*)s->W1, (double*)S, N, nt, ncols, sst);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "project: %s", cudaGetErrorString(e));
+  PROJECT_TRY(space_mass_solve_f64(target, S, cs));
+  if (s->prec == SGM_F32) {
+    const long nv = total * R;
+    k_narrow_copy<float><<<(unsigned)std::min<long>((nv + 255) / 256, 152L * 16), 256, 0, cs>>>((const double*)S, (float*)out_hat, nv);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "project: %s", cudaGetErrorString(e));
+  }
   return SGM_OK;
 }

@@ -449,6 +449,15 @@ template <typename T> int backward_impl(sgm_space* s, const void* uh, void* u, c
 
 int sgm::space_check(const sgm_space* s) { return check_space(s); }
 
+// The mass solve of the forward transform (a = 0 systems) on FP64 spectral data of any space
+// with a Shen basis on axis 0, in place: B u = data.
+int sgm::space_mass_solve_f64(sgm_space* s, void* data, cudaStream_t st) {
+  const int k = s->kinds[0];
+  if (k == SGM_SHEN_DIRICHLET || k == SGM_LEGENDRE_DIRICHLET)
+    return solve_impl<double>(s, kDirichlet, 0.0, 1.0, 0.0, data, data, st);
+  return solve_impl<double>(s, kBiharmonic, 0.0, 0.0, 1.0, data, data, st);
+}
+
 namespace {
 
 void free_space(sgm_space* s) {

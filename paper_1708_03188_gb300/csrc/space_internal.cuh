@@ -51,6 +51,9 @@ namespace sgm {
 // precision (nullptr if L has no compiled kernel); owned by the space
 int need_twf(sgm_space* s, int L, const void** out);
 int space_check(const sgm_space* s);
+// mass solve B u = data in place on FP64 spectral data of a space whose axis 0 is a Shen basis
+// (space.cu; uses the space's elimination scratch)
+int space_mass_solve_f64(sgm_space* s, void* data, cudaStream_t st);
 // device table of the compile-time FFT engine for length L (caller frees)
 int make_fast_twiddles(int precision, int L, void** out);
 // stencil coefficient table of sgm_project_dx for a space with a Chebyshev axis (project.cu);

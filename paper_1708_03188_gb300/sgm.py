@@ -38,6 +38,7 @@ _SIGNATURES = {
     "sgm_helmholtz": (ctypes.c_int, [_VP, _D, _D, _VP, _VP, _VP]),
     "sgm_biharmonic": (ctypes.c_int, [_VP, _D, _D, _D, _VP, _VP, _VP]),
     "sgm_project_dx": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP]),
+    "sgm_project": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "sgm_gl_create": (ctypes.c_int, [ctypes.POINTER(_VP), _VP, _D, _D, _D, _D, ctypes.c_int]),
     "sgm_gl_destroy": (ctypes.c_int, [_VP]),
     "sgm_gl_rhs": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -227,6 +228,17 @@ class Space:
             out = self.empty_spectral(u_hat.device)
         self._check(out, self.spectral_shape, self.spectral_dtype, "out")
         check(lib().sgm_project_dx(self._h, int(axis), int(order), _ptr(u_hat), _ptr(out), _stream(stream)))
+        return out
+
+    def project(self, u_hat, axis, order, target, out=None, stream=None):
+        """project(Dx(u, axis, order), target) (Sec. 5) onto a target Space that differs from
+        this one at most in the basis of axis 0 (regular or Shen, same family): the Galerkin
+        projection's coefficients in ``target``'s spectral layout."""
+        self._check(u_hat, self.spectral_shape, self.spectral_dtype, "u_hat")
+        if out is None:
+            out = target.empty_spectral(u_hat.device)
+        target._check(out, target.spectral_shape, target.spectral_dtype, "out")
+        check(lib().sgm_project(self._h, int(axis), int(order), _ptr(u_hat), target._h, _ptr(out), _stream(stream)))
         return out
 
     def chebyshev_space(self):

@@ -157,3 +157,98 @@ def test_project_dx_ignores_rows_past_the_basis():
     clean[6:] = 0
     for axis, m in ((0, 1), (1, 1), (0, 0)):
         assert np.array_equal(sp.project_dx(u_hat, axis, m), sp.project_dx(clean, axis, m))
+
+
+# ---- projection onto a Shen space (Sec. 5 project with a composite target basis) ---------------
+def cheb_poly(k):
+    """Monomial coefficients of T_k (three-term recurrence, exact)."""
+    a, b = [Fraction(1)], [Fraction(0), Fraction(1)]
+    if k == 0:
+        return a
+    for _ in range(k - 1):
+        a, b = b, [x - y for x, y in zip([Fraction(0)] + [2 * v for v in b] + [Fraction(0)],
+                                        a + [Fraction(0)] * 3)][:len(b) + 1]
+    return b
+
+
+def weighted_moment(n):
+    """int_{-1}^{1} x^n (1 - x^2)^(-1/2) dx / pi = (n-1)!!/n!! for even n, 0 for odd n."""
+    if n % 2:
+        return Fraction(0)
+    v = Fraction(1)
+    for j in range(1, n, 2):
+        v *= Fraction(j, j + 1)
+    return v
+
+
+def inner_w(p, q):
+    """(p, q)_w / pi for monomial coefficient lists, exactly."""
+    return sum(a * b * weighted_moment(i + j) for i, a in enumerate(p) for j, b in enumerate(q) if a and b)
+
+
+def shen_poly(kind, k):
+    """Monomial coefficients of the Chebyshev-family basis function psi_k of ``kind``."""
+    P = quadrature.basis_coefficients(kind, k + 5)[k]
+    out = [Fraction(0)] * (k + 5)
+    for j, c in enumerate(P):
+        if c:
+            cf = Fraction(c).limit_denominator(1000)
+            for i, t in enumerate(cheb_poly(j)):
+                out[i] += cf * t
+    return out
+
+
+def solve_exact(A, b):
+    """Gauss-Jordan elimination in Fractions."""
+    n = len(b)
+    M = [row[:] + [b[i]] for i, row in enumerate(A)]
+    for c in range(n):
+        piv = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[piv] = M[piv], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [x - f * y for x, y in zip(M[r], M[c])]
+    return [M[i][n] / M[i][i] for i in range(n)]
+
+
+@pytest.mark.parametrize("target", ["dirichlet", "biharmonic"])
+@pytest.mark.parametrize("kind", ["chebyshev", "dirichlet", "biharmonic"])
+def test_project_dx_onto_shen_space_exact_galerkin(kind, target):
+    # The projection of p^(m) onto the Shen space W is the w-orthogonal (Galerkin) projection:
+    # coefficients c with sum_j c_j (psi_j, psi_k)_w = (p^(m), psi_k)_w for every k.  Here every
+    # inner product is an exact rational multiple of pi (Chebyshev-weight moments of monomials),
+    # and the system is solved in Fractions: no quadrature, no NumPy series code.
+    N = 10
+    g = np.random.default_rng(31)
+    bc = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2}[kind]
+    q = [Fraction(int(v)) for v in g.integers(-9, 10, N - 2 * bc)]
+    p = q
+    for _ in range(bc):
+        p = poly_mul(p, [Fraction(1), Fraction(0), Fraction(-1)])
+    sp = Space([kind], [N])
+    x, _ = quadrature.gauss_points(N)
+    u_hat = sp.forward(poly_eval(p, x))
+    nt = quadrature.num_basis(target, N)
+    psi = [shen_poly(target, k) for k in range(nt)]
+    B = [[inner_w(psi[j], psi[k]) for j in range(nt)] for k in range(nt)]
+    for m in range(4):
+        dp = poly_der(p, m)
+        exact = solve_exact(B, [inner_w(dp, psi[k]) for k in range(nt)])
+        exact = np.array([float(v) for v in exact] + [0.0] * (N - nt))
+        got = sp.project_dx(u_hat, 0, m, target=target)
+        scale = max(np.max(np.abs(exact)), 1.0)
+        assert np.max(np.abs(got - exact)) < 1e-11 * scale, (kind, target, m)
+
+
+def test_project_onto_shen_space_keeps_members():
+    # a function already in W projects onto itself: biharmonic phi_l satisfy the Dirichlet
+    # conditions, so their projection onto the Dirichlet space reproduces them exactly
+    N = 12
+    bs = Space(["biharmonic", "c2c"], [N, 4])
+    ds = Space(["dirichlet", "c2c"], [N, 4])
+    g = inputs.rng("box3d", 43)
+    u_hat = np.zeros((N, 4), complex)
+    u_hat[:N - 4] = g.standard_normal((N - 4, 4)) + 1j * g.standard_normal((N - 4, 4))
+    w = bs.project_dx(u_hat, 0, 0, target="dirichlet")
+    assert np.allclose(ds.backward(w), bs.backward(u_hat), rtol=0, atol=1e-13)

@@ -153,3 +153,60 @@ def test_project_dx_errors():
         gs.project_dx(x, 0, 1, out=x)                 # in place is refused
     w0 = gs.chebyshev_space()
     assert w0.kinds == ("chebyshev", "c2c") and w0.spectral_shape == gs.spectral_shape
+
+
+# ---- projection onto a Shen space: sgm_project (Sec. 5 project with a composite target) -----------
+PROJECT_CASES = [
+    (["dirichlet"], [16], "biharmonic"),
+    (["biharmonic"], [33], "dirichlet"),
+    (["chebyshev"], [24], "dirichlet"),
+    (["chebyshev", "r2c"], [24, 16], "biharmonic"),
+    (["dirichlet", "c2c", "r2c"], [20, 8, 12], "dirichlet"),
+    (["biharmonic", "c2c", "r2c"], [40, 6, 10], "dirichlet"),
+    (["dirichlet", "c2c"], [64, 5], "biharmonic"),
+    (["legendre_dirichlet", "r2c"], [18, 8], "legendre_biharmonic"),
+    (["legendre_biharmonic", "c2c", "r2c"], [22, 4, 6], "legendre_dirichlet"),
+]
+# FP32: the derivative's regular coefficients are rounded to FP32 once before the (FP64)
+# Galerkin projection, whose coefficient-space condition grows with the target's mass matrix
+PROJECT_TOL = {"f64": 1e-11, "f32": 2.0 ** -18}
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+@pytest.mark.parametrize("kinds,sizes,target", PROJECT_CASES)
+def test_project_onto_shen_space(kinds, sizes, target, prec):
+    sp = gspace(kinds, sizes, prec)
+    tk = [target] + list(kinds[1:])
+    tg = gspace(tk, sizes, prec)
+    osp = OSpace(kinds, sizes)
+    uh = random_coefficients(sp, 60 + len(sizes))
+    ud = to_dev(uh, sp.spectral_dtype)
+    uh_used = to_np(ud)
+    worst = 0.0
+    for axis in range(len(kinds)):
+        for m in (0, 1, 2):
+            got = to_np(sp.project(ud, axis, m, tg))
+            ref = osp.project_dx(uh_used, axis, m, target=target)
+            e = rel(got, ref)
+            worst = max(worst, e)
+            assert e < PROJECT_TOL[prec], (axis, m, e)
+            nt = sizes[0] - (2 if "dirichlet" in target else 4)
+            assert np.all(got[nt:] == 0)
+    print(f"project {kinds} {sizes} -> {target} {prec}: worst {worst:.2e}")
+    sp.close()
+    tg.close()
+
+
+def test_project_rejects_mismatched_targets():
+    from paper_1708_03188_gb300.sgm import SgmError
+    sp = gspace(["dirichlet", "c2c"], [16, 8], "f64")
+    u = sp.empty_spectral().zero_()
+    for kinds, sizes, prec in ((["biharmonic", "c2c"], [16, 9], "f64"), (["biharmonic", "c2c"], [16, 8], "f32"),
+                               (["legendre_biharmonic", "c2c"], [16, 8], "f64"), (["biharmonic", "r2c"], [16, 14], "f64")):
+        tg = gspace(kinds, sizes, prec)
+        out = tg.empty_spectral()
+        with pytest.raises((SgmError, ValueError)):
+            from paper_1708_03188_gb300 import sgm
+            sgm.check(sgm.lib().sgm_project(sp._h, 0, 1, sgm._ptr(u), tg._h, sgm._ptr(out), sgm._stream(None)))
+        tg.close()
+    sp.close()
