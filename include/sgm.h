@@ -77,6 +77,12 @@ extern "C" {
 #define SGM_LEGENDRE 5             /* L_k, k = 0..N-1 */
 #define SGM_LEGENDRE_DIRICHLET 6   /* L_k - L_{k+2}, k = 0..N-3 */
 #define SGM_LEGENDRE_BIHARMONIC 7  /* L_k - 2(2k+5)/(2k+7) L_{k+2} + (2k+3)/(2k+7) L_{k+4}, k = 0..N-5 */
+/* Shen Neumann basis (Sec. 3.1 lists ShenNeumannBasis without its formula; this is the
+ * combination with phi_k'(+-1) = 0), axis 0 only, N >= 4.  Its Helmholtz solve (sgm_helmholtz_solve,
+ * sgm_helmholtz) handles a Fourier column whose system has no zeroth-order term (b - a kappa2
+ * evaluates to exactly 0, e.g. the constant column of a Poisson problem) by setting u_hat_0 = 0
+ * and dropping the equation of phi_0: u is then fixed up to the constant it cannot see. */
+#define SGM_SHEN_NEUMANN 8         /* T_k - (k/(k+2))^2 T_{k+2}, k = 0..N-3 */
 
 /* precision */
 #define SGM_F32 1                /* FP32 transforms, FP64 eliminations */
@@ -100,7 +106,15 @@ const char* sgm_status_string(int status);
  * Create a tensor-product space (the TensorProductSpace of Sec. 4; bases of Sec. 3.1).
  *   out        receives the new space.
  *   ndim       1..3.
- *   kinds      ndim basis kinds (see above).
+ *   kinds      ndim basis kinds (see above), in the order of the array axes.  The canonical
+ *              order puts the Chebyshev or Legendre axis first and the R2C axis last; any other
+ *              order (the axes option of Sec. 4, e.g. TensorProductSpace((K1, K0), axes=(1, 0))
+ *              with the Dirichlet basis along the second axis) gives a view of the canonical
+ *              space whose arrays are axis permutations of the canonical ones: every call
+ *              permutes its input into a canonical workspace, runs the canonical call and
+ *              permutes the result back (two extra passes over the data).  At most one
+ *              polynomial and one R2C axis.  Axis arguments (sgm_project_dx, sgm_project) and
+ *              shapes (sgm_space_shape) follow the array order.
  *   n          ndim sizes: quadrature points per axis (N >= 4 for Dirichlet, 6 <= N <= 2048
  *              for biharmonic, N <= 1024 for the Legendre bases; Fourier sizes >= 1).  Every
  *              size <= 4096.

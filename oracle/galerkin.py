@@ -62,11 +62,15 @@ def biharmonic_matrix(mats, a, b, c, kappa2):
     return a * (S - 2.0 * kappa2 * A + kappa2 * kappa2 * B) + b * (A - kappa2 * B) + c * B
 
 
-def solve_columns(kind, N, rhs, kappa2, system):
+def solve_columns(kind, N, rhs, kappa2, system, singular=None):
     """Solve system(kappa2) u = rhs along axis 0 for every column.
 
     rhs has shape (N, ...) with the valid entries in rows 0..nb-1; kappa2 has
     the shape of rhs[0].  Rows nb..N-1 of the result are zero.
+
+    singular(kappa2) -> bool marks columns whose system has the constant phi_0 in its
+    null space (the Neumann basis with no zeroth-order term): there u_hat_0 = 0 and the
+    equation of the test function phi_0 (the compatibility condition) is dropped.
     """
     nb = quadrature.num_basis(kind, N)
     rhs = np.asarray(rhs)
@@ -74,5 +78,9 @@ def solve_columns(kind, N, rhs, kappa2, system):
     k2 = np.broadcast_to(kappa2, rhs.shape[1:]).reshape(-1)
     out = np.zeros(cols.shape, dtype=np.result_type(cols.dtype, np.float64))
     for c in range(cols.shape[1]):
-        out[:nb, c] = np.linalg.solve(system(k2[c]), cols[:nb, c])
+        M = system(k2[c])
+        if singular is not None and singular(k2[c]):
+            out[1:nb, c] = np.linalg.solve(M[1:, 1:], cols[1:nb, c])
+        else:
+            out[:nb, c] = np.linalg.solve(M, cols[:nb, c])
     return out.reshape(rhs.shape)

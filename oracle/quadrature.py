@@ -4,6 +4,9 @@ Chebyshev family, Sec. 3.4.2 of the paper: the Chebyshev-Gauss points
 x_j = cos((2j+1) pi / (2N)) and the constant weights w_j = pi / N, and the Shen
 composite bases
   Dirichlet   phi_l = T_l - T_{l+2},                                   l = 0..N-3  (Eq. chebdirichlet)
+  Neumann     phi_l = T_l - (l/(l+2))^2 T_{l+2},                       l = 0..N-3
+              (Sec. 3.1 lists ShenNeumannBasis without its formula; this is Shen's
+              Neumann basis, the combination with phi_l'(+-1) = 0, since T_n'(+-1) = (+-1)^(n+1) n^2)
   biharmonic  phi_l = T_l - 2(l+2)/(l+3) T_{l+2} + (l+1)/(l+3) T_{l+4}, l = 0..N-5  (Eq. chebbiharmonic)
   regular     phi_l = T_l,                                             l = 0..N-1
 Legendre family (Sec. 3.1 lists the bases; Sec. 3.4.2 and Sec. 4 give the composite ones): the
@@ -22,7 +25,7 @@ import numpy as np
 from numpy.polynomial import chebyshev as npcheb
 from numpy.polynomial import legendre as npleg
 
-CHEBYSHEV_KINDS = ("chebyshev", "dirichlet", "biharmonic")
+CHEBYSHEV_KINDS = ("chebyshev", "dirichlet", "neumann", "biharmonic")
 LEGENDRE_KINDS = ("legendre", "legendre_dirichlet", "legendre_biharmonic")
 KINDS = CHEBYSHEV_KINDS + LEGENDRE_KINDS
 
@@ -58,7 +61,7 @@ def points(kind, N):
 
 def num_basis(kind, N):
     """Number of basis functions: N, N-2 (index set l^D) or N-4 (index set l^B)."""
-    return {"chebyshev": N, "dirichlet": N - 2, "biharmonic": N - 4,
+    return {"chebyshev": N, "dirichlet": N - 2, "neumann": N - 2, "biharmonic": N - 4,
             "legendre": N, "legendre_dirichlet": N - 2, "legendre_biharmonic": N - 4}[kind]
 
 
@@ -70,6 +73,8 @@ def basis_coefficients(kind, N):
         P[l, l] = 1.0
         if kind in ("dirichlet", "legendre_dirichlet"):
             P[l, l + 2] = -1.0
+        elif kind == "neumann":
+            P[l, l + 2] = -(l / (l + 2.0)) ** 2
         elif kind == "biharmonic":
             P[l, l + 2] = -2.0 * (l + 2) / (l + 3)
             P[l, l + 4] = (l + 1) / (l + 3)

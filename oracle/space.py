@@ -133,10 +133,15 @@ class Space:
         return out.real if self.real else out
 
     def helmholtz(self, a, b, f_tilde):
-        """Solve the weak form of a lap(u) + b u = f, given S(F(f)) (Eq. laplace)."""
+        """Solve the weak form of a lap(u) + b u = f, given S(F(f)) (Eq. laplace).
+
+        Neumann basis: a column with b - a kappa2 = 0 (pure Poisson in the constant Fourier mode)
+        determines u only up to a constant; there u_hat_0 = 0 and the phi_0 equation is dropped.
+        """
         mats = self.matrices()
+        singular = (lambda k2: b - a * k2 == 0.0) if self.kinds[0] == "neumann" else None
         return galerkin.solve_columns(self.kinds[0], self.sizes[0], f_tilde, self.kappa2(),
-                                      lambda k2: galerkin.helmholtz_matrix(mats, a, b, k2))
+                                      lambda k2: galerkin.helmholtz_matrix(mats, a, b, k2), singular)
 
     def biharmonic(self, a, b, c, f_tilde):
         """Solve the weak form of a lap^2(u) + b lap(u) + c u = f, given S(F(f))."""

@@ -47,7 +47,16 @@ struct FftPlan {
 };
 
 // ---- Shen basis kinds (mirror of sgm.h) -------------------------------------------------
-enum Basis { kCheb = 0, kDirichlet = 1, kBiharmonic = 2, kC2C = 3, kR2C = 4 };
+enum Basis { kCheb = 0, kDirichlet = 1, kBiharmonic = 2, kC2C = 3, kR2C = 4, kNeumann = 8 };
+// Shen Neumann basis phi_k = T_k - q_k T_{k+2}, q_k = (k / (k + 2))^2
+template <typename T> __host__ __device__ __forceinline__ T neumann_q(int k) {
+  const T r = (T)k / (T)(k + 2);
+  return r * r;
+}
+// number of basis functions of a Chebyshev-family axis of N points
+__host__ __device__ __forceinline__ int basis_count(int basis, int N) {
+  return (basis == kDirichlet || basis == kNeumann) ? N - 2 : (basis == kBiharmonic ? N - 4 : N);
+}
 
 // Fourier wavenumber layout of the columns of a spectral array (used by the solves):
 // a column index c = i1 * n2 + i2 (3-D) or c = i2 (2-D) or c = 0 (1-D);
@@ -119,11 +128,16 @@ std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N);
 // the same image of any N x N matrix P (row-major, row = output row), N <= kTcMaxN
 std::vector<uint16_t> tc_matrix_image(const std::vector<long double>& P, int N);
 int tc_timeouts(bool reset);
+int stream_timeouts(bool reset);   // k_stream.cu
 int cnn_tc_timeouts(bool reset);   // k_cnn_tc.cu
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out,
                          int N, long ncols, const Wavenumbers& wn, const double* tab, double* scratch,
                          long scratch_threads, const int2* groups, long ngroups, cudaStream_t s);
+// the same solve on FP64 spectral input (complex) with the solution rounded once to complex64
+cudaError_t launch_solve_f64_to_f32(int basis, double a, double b, double c, const void* in, void* out, int N, long ncols,
+                                    const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
+                                    const int2* groups, long ngroups, cudaStream_t s);
 
 }  // namespace sgm

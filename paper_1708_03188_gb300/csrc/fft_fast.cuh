@@ -145,6 +145,78 @@ __device__ __forceinline__ void fft_fast(C* buf, int nlines, const C* __restrict
   fast_passes<L, 1, 0, LINES, NTHREADS, INV>(buf, nlines, tw, typename FastRadices<L>::type{});
 }
 
+// ---- the same passes with other shared-memory layouts ------------------------------------------
+// A pass reads its inputs through ld_at(line, e) from `src` and writes its outputs through
+// st_at(line, e) to `dst` (src may equal dst: every input is read before the synchronisation
+// that precedes the writes).  With COLS the butterflies of a warp run across lines first (line =
+// b % LINES), which suits the column-tile layout e * LINES + line written by a TMA box of LINES
+// neighbouring columns: a warp then touches consecutive words in every load and store, with no
+// padding.  Without COLS the mapping is that of fast_pass (line = b / (L / R)).
+template <int L, int R, int NS, int TWO, int LINES, int NTHREADS, bool INV, bool COLS, typename C, typename LA,
+          typename SA>
+__device__ __forceinline__ void gen_pass(const C* src, C* dst, const C* __restrict__ tw, LA ld_at, SA st_at) {
+  constexpr int LR = L / R;
+  constexpr int TOTAL = LINES * LR;
+  constexpr int M = (TOTAL + NTHREADS - 1) / NTHREADS;
+  C v[M][R];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int b = threadIdx.x + m * NTHREADS;
+    if (b < TOTAL) {
+      const int line = COLS ? b % LINES : b / LR, j = COLS ? b / LINES : b % LR;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[m][r] = src[ld_at(line, j + r * LR)];
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int b = threadIdx.x + m * NTHREADS;
+    if (b < TOTAL) {
+      const int line = COLS ? b % LINES : b / LR, j = COLS ? b / LINES : b % LR;
+      const int k = j % NS;
+      if (NS > 1) {
+        const C* t = tw + TWO + k * R;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+          C w = __ldg(&t[r]);
+          if (INV) w.y = -w.y;
+          v[m][r] = cmul(v[m][r], w);
+        }
+      }
+      butterfly_any<R, INV>(v[m]);
+      const int base = (j - k) * R + k;
+#pragma unroll
+      for (int q = 0; q < R; ++q) dst[st_at(line, base + q * NS)] = v[m][q];
+    }
+  }
+  __syncthreads();
+}
+
+template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, bool COLS, bool FIRST, typename C, typename LA0,
+          typename AT>
+__device__ __forceinline__ void gen_passes(const C*, C*, const C*, LA0, AT, Radices<>) {}
+
+template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, bool COLS, bool FIRST, typename C, typename LA0,
+          typename AT, int R, int... Rest>
+__device__ __forceinline__ void gen_passes(const C* src, C* buf, const C* tw, LA0 ld0, AT at, Radices<R, Rest...>) {
+  if constexpr (FIRST)
+    gen_pass<L, R, NS, TWO, LINES, NTHREADS, INV, COLS>(src, buf, tw, ld0, at);
+  else
+    gen_pass<L, R, NS, TWO, LINES, NTHREADS, INV, COLS>(buf, buf, tw, at, at);
+  gen_passes<L, NS * R, TWO + NS * R, LINES, NTHREADS, INV, COLS, false>(src, buf, tw, ld0, at, Radices<Rest...>{});
+}
+
+// Transform of LINES lines in the column-tile layout buf[e * LINES + line], in place.  The first
+// pass reads input e of a line from position first(e) instead (for example a reordering), so the
+// caller need not move the data beforehand.  Ends with __syncthreads().
+template <int L, int LINES, int NTHREADS, bool INV, typename C, typename FM>
+__device__ __forceinline__ void fft_cols(C* buf, const C* __restrict__ tw, FM first) {
+  auto at = [](int line, int e) { return e * LINES + line; };
+  auto ld0 = [first](int line, int e) { return first(e) * LINES + line; };
+  gen_passes<L, 1, 0, LINES, NTHREADS, INV, true, true>(buf, buf, tw, ld0, at, typename FastRadices<L>::type{});
+}
+
 // Host: number of entries of the pass tables of length L (sum over passes of NS * R).
 inline int fast_table_size(int L) {
   int rs[8], np = 0;

@@ -3,6 +3,7 @@
 // Scalar product (the inner product S of Sec. 3.4.2, computed "with a DCT"):
 //   moments  t_k = (pi/N) sum_j g_j cos(pi k (2j+1) / (2N))        (DCT-II, weights pi/N)
 //   stencil  Dirichlet  S_k = t_k - t_{k+2},                         k = 0..N-3
+//            Neumann    S_k = t_k - q_k t_{k+2}, q_k = (k/(k+2))^2,    k = 0..N-3
 //            biharmonic S_k = t_k + beta_k t_{k+2} + gamma_k t_{k+4}, k = 0..N-5,
 //            beta_k = -2(k+2)/(k+3), gamma_k = (k+1)/(k+3)          (Eq. chebbiharmonic)
 //            regular    S_k = t_k
@@ -12,7 +13,7 @@
 // w_k = exp(-i pi k / (2N))  (Makhoul's reordering).
 //
 // Backward (Eq. fast_shen): the stencil maps Shen coefficients to Chebyshev coefficients
-//   Dirichlet a_k = c_k - c_{k-2};  biharmonic a_k = c_k + beta_{k-2} c_{k-2} + gamma_{k-4} c_{k-4}
+//   Dirichlet a_k = c_k - c_{k-2};  Neumann a_k = c_k - q_{k-2} c_{k-2};  biharmonic a_k = c_k + beta_{k-2} c_{k-2} + gamma_{k-4} c_{k-4}
 // and the DCT-III u_j = sum_k a_k cos(pi k (2j+1) / (2N)) is one inverse FFT of
 // V_0 = a_0, V_k = conj(w_k) (a_k - i a_{N-k}) / 2 (k >= 1), undoing the reordering.
 //
@@ -37,7 +38,7 @@ template <typename T> __device__ __forceinline__ T bih_beta(int k) { return (T)(
 template <typename T> __device__ __forceinline__ T bih_gamma(int k) { return (T)(k + 1) / (T)(k + 3); }
 
 __device__ __forceinline__ int nbasis(int basis, int N) {
-  return basis == kDirichlet ? N - 2 : (basis == kBiharmonic ? N - 4 : N);
+  return basis_count(basis, N);
 }
 
 template <typename T, int MODE, typename TS>
@@ -107,6 +108,9 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
           s = m[k];
         } else if (basis == kDirichlet) {
           s = csub(m[k], m[k + 2]);
+        } else if (basis == kNeumann) {
+          const T q = neumann_q<T>(k);
+          s = mk<C>(m[k].x - q * m[k + 2].x, m[k].y - q * m[k + 2].y);
         } else {
           const T be = bih_beta<T>(k), ga = bih_gamma<T>(k);
           s = mk<C>(m[k].x + be * m[k + 2].x + ga * m[k + 4].x, m[k].y + be * m[k + 2].y + ga * m[k + 4].y);
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(256) k_cheb(const void* __restrict__ in, void*
       C a = c[k];
       if (basis == kDirichlet) {
         if (k >= 2) a = csub(a, c[k - 2]);
+      } else if (basis == kNeumann) {
+        if (k >= 2) { const T q = neumann_q<T>(k - 2); a.x -= q * c[k - 2].x; a.y -= q * c[k - 2].y; }
       } else if (basis == kBiharmonic) {
         if (k >= 2) { const T be = bih_beta<T>(k - 2); a.x += be * c[k - 2].x; a.y += be * c[k - 2].y; }
         if (k >= 4) { const T ga = bih_gamma<T>(k - 4); a.x += ga * c[k - 4].x; a.y += ga * c[k - 4].y; }

@@ -214,6 +214,10 @@ long double cheb_T(long k, long j, long N) {
 long double shen_phi(int basis, long k, long j, long N) {
   if (basis == kCheb) return cheb_T(k, j, N);
   if (basis == kDirichlet) return cheb_T(k, j, N) - cheb_T(k + 2, j, N);
+  if (basis == kNeumann) {
+    const long double r = (long double)k / (long double)(k + 2);
+    return cheb_T(k, j, N) - r * r * cheb_T(k + 2, j, N);
+  }
   const long double be = -2.0L * (k + 2) / (k + 3), ga = (long double)(k + 1) / (k + 3);
   return cheb_T(k, j, N) + be * cheb_T(k + 2, j, N) + ga * cheb_T(k + 4, j, N);
 }
@@ -244,7 +248,7 @@ std::vector<uint16_t> tc_matrix_image(const std::vector<long double>& P, int N) 
 }
 
 std::vector<uint16_t> tc_cheb_image(int mode, int basis, int N) {
-  const int nb = basis == kDirichlet ? N - 2 : basis == kBiharmonic ? N - 4 : N;
+  const int nb = basis_count(basis, N);
   const long double pi = 3.141592653589793238462643383279502884L;
   std::vector<long double> P((size_t)N * N, 0.0L);
   for (int n = 0; n < N; ++n)

@@ -148,6 +148,139 @@ __global__ void __launch_bounds__(kFastThreads) k_strided_fast(const cplx<T>* in
 template <typename T> __device__ __forceinline__ T fbeta(int k) { return (T)(-2 * (k + 2)) / (T)(k + 3); }
 template <typename T> __device__ __forceinline__ T fgamma(int k) { return (T)(k + 1) / (T)(k + 3); }
 
+// position of input point j in the even/odd (Makhoul) reordering of a length-N line
+template <int N> __device__ __forceinline__ int cheb_reord(int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
+
+// Element (line t, position e) of a tile of TW lines: the padded layout of fft_fast
+// (t * pad_ld(N) + padi(e), threads over positions first) or, with COLS, the column-tile layout of
+// fft_cols (e * TW + t, threads over lines first).
+template <bool COLS, int N, int TW> struct TileIdx {
+  __device__ __forceinline__ static int at(int t, int e) { return COLS ? e * TW + t : t * pad_ld(N) + padi(e); }
+  __device__ __forceinline__ static int line(int idx) { return COLS ? idx % TW : idx / N; }
+  __device__ __forceinline__ static int pos(int idx) { return COLS ? idx / TW : idx % N; }
+};
+
+// Forward Chebyshev pass after the FFT of the reordered lines in `buf`: DCT moments in place,
+// then the Shen stencil of `basis`, written to `out` at rows k, columns t0 + t (t < nt).
+template <typename T, int MODE, typename TS, int N, bool COLS = false>
+__device__ __forceinline__ void cheb_forward_finish(cplx<T>* buf, int nt, long t0, long inner, int basis, int real,
+                                                    void* __restrict__ out, const cplx<T>* __restrict__ dctw) {
+  using C = cplx<T>;
+  constexpr int TW = fast_tw_cols<T>();
+  using I = TileIdx<COLS, N, TW>;
+  constexpr int PER = (N * TW + kFastThreads - 1) / kFastThreads;   // elements per thread
+  const int nb = basis_count(basis, N);
+  // moments, computed in registers and written back in place
+  const T scale = (MODE == kChebScalar) ? (T)3.14159265358979323846 / (T)N : (T)2 / (T)N;
+  C m[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) {
+      const C v = buf[I::at(t, k)];
+      const C vr = cconj(buf[I::at(t, k == 0 ? 0 : N - k)]);
+      const C w = __ldg(&dctw[k]);
+      const C a = cadd(v, vr), b = csub(v, vr);
+      T sc = scale;
+      if (MODE == kChebForwardT && k == 0) sc *= (T)0.5;
+      m[q] = mk<C>((T)0.5 * sc * (w.x * a.x - w.y * a.y), (T)0.5 * sc * (w.x * b.y + w.y * b.x));
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) buf[I::at(t, k)] = m[q];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
+    const int k = idx / TW, t = idx % TW;
+    if (t >= nt) continue;
+    C s = mk<C>((T)0, (T)0);
+    if (k < nb) {
+      if (MODE == kChebForwardT || basis == kCheb) {
+        s = buf[I::at(t, k)];
+      } else if (basis == kDirichlet) {
+        s = csub(buf[I::at(t, k)], buf[I::at(t, k + 2)]);
+      } else if (basis == kNeumann) {
+        const T q = neumann_q<T>(k);
+        const C a0 = buf[I::at(t, k)], a2 = buf[I::at(t, k + 2)];
+        s = mk<C>(a0.x - q * a2.x, a0.y - q * a2.y);
+      } else {
+        const T be = fbeta<T>(k), ga = fgamma<T>(k);
+        const C a0 = buf[I::at(t, k)], a2 = buf[I::at(t, k + 2)], a4 = buf[I::at(t, k + 4)];
+        s = mk<C>(a0.x + be * a2.x + ga * a4.x, a0.y + be * a2.y + ga * a4.y);
+      }
+    }
+    const long g = (long)k * inner + t0 + t;
+    if (MODE == kChebForwardT) {
+      if (real) reinterpret_cast<T*>(out)[g] = s.x; else reinterpret_cast<C*>(out)[g] = s;
+    } else {
+      to_spec<TS, C>(reinterpret_cast<TS*>(out), g, real, s);
+    }
+  }
+}
+
+// Backward Chebyshev pass before the inverse FFT: `buf` holds the coefficient rows k < nb of
+// each line (zero past them); applies the Shen stencil (Eq. fast_shen) and the DCT-III
+// pre-twiddle in place.  Ends with __syncthreads().
+template <typename T, int N, bool COLS = false>
+__device__ __forceinline__ void cheb_backward_prepare(cplx<T>* buf, int nt, int basis, const cplx<T>* __restrict__ dctw) {
+  using C = cplx<T>;
+  using I = TileIdx<COLS, N, fast_tw_cols<T>()>;
+  constexpr int PER = (N * fast_tw_cols<T>() + kFastThreads - 1) / kFastThreads;
+  C a[PER];
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) {
+      C v = buf[I::at(t, k)];
+      if (basis == kDirichlet) {
+        if (k >= 2) v = csub(v, buf[I::at(t, k - 2)]);
+      } else if (basis == kNeumann) {
+        if (k >= 2) { const T q = neumann_q<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x -= q * u.x; v.y -= q * u.y; }
+      } else if (basis == kBiharmonic) {
+        if (k >= 2) { const T be = fbeta<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x += be * u.x; v.y += be * u.y; }
+        if (k >= 4) { const T ga = fgamma<T>(k - 4); const C u = buf[I::at(t, k - 4)]; v.x += ga * u.x; v.y += ga * u.y; }
+      }
+      a[q] = v;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) buf[I::at(t, k)] = a[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) {
+      if (k == 0) {
+        a[q] = buf[I::at(t, 0)];
+      } else {
+        const C x = buf[I::at(t, k)], y = buf[I::at(t, N - k)];
+        const C d = mk<C>(x.x + y.y, x.y - y.x);
+        a[q] = cscale(cmulc(d, __ldg(&dctw[k])), (T)0.5);
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = I::line(idx), k = I::pos(idx);
+    if (t < nt) buf[I::at(t, k)] = a[q];
+  }
+  __syncthreads();
+}
+
 template <typename T, int MODE, typename TS, int N>
 __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restrict__ in, void* __restrict__ out,
                                                             long inner, int basis, int real,
@@ -156,13 +289,11 @@ __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restri
   using C = cplx<T>;
   constexpr int TW = fast_tw_cols<T>();
   constexpr int LDP = pad_ld(N);
-  constexpr int PER = (N * TW + kFastThreads - 1) / kFastThreads;   // elements per thread
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const long t0 = (long)blockIdx.x * TW;
   const int nt = (int)min((long)TW, inner - t0);
-  const int nb = basis == kDirichlet ? N - 2 : (basis == kBiharmonic ? N - 4 : N);
-  auto reord = [](int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); };
+  const int nb = basis_count(basis, N);
 
   if (MODE == kChebScalar || MODE == kChebForwardT) {
     staged_copy<N * TW, C>(
@@ -174,58 +305,11 @@ __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restri
         },
         [&](int idx, C v) {
           const int j = idx / TW, t = idx % TW;
-          if (t < nt) buf[t * LDP + padi(reord(j))] = v;
+          if (t < nt) buf[t * LDP + padi(cheb_reord<N>(j))] = v;
         });
     __syncthreads();
     fft_fast<N, TW, kFastThreads, false>(buf, nt, twf);
-    // moments, computed in registers and written back in place
-    const T scale = (MODE == kChebScalar) ? (T)3.14159265358979323846 / (T)N : (T)2 / (T)N;
-    C m[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) {
-        const C v = buf[t * LDP + padi(k)];
-        const C vr = cconj(buf[t * LDP + padi(k == 0 ? 0 : N - k)]);
-        const C w = __ldg(&dctw[k]);
-        const C a = cadd(v, vr), b = csub(v, vr);
-        T sc = scale;
-        if (MODE == kChebForwardT && k == 0) sc *= (T)0.5;
-        m[q] = mk<C>((T)0.5 * sc * (w.x * a.x - w.y * a.y), (T)0.5 * sc * (w.x * b.y + w.y * b.x));
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) buf[t * LDP + padi(k)] = m[q];
-    }
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
-      const int k = idx / TW, t = idx % TW;
-      if (t >= nt) continue;
-      const C* mm = buf + t * LDP;
-      C s = mk<C>((T)0, (T)0);
-      if (k < nb) {
-        if (MODE == kChebForwardT || basis == kCheb) {
-          s = mm[padi(k)];
-        } else if (basis == kDirichlet) {
-          s = csub(mm[padi(k)], mm[padi(k + 2)]);
-        } else {
-          const T be = fbeta<T>(k), ga = fgamma<T>(k);
-          const C a0 = mm[padi(k)], a2 = mm[padi(k + 2)], a4 = mm[padi(k + 4)];
-          s = mk<C>(a0.x + be * a2.x + ga * a4.x, a0.y + be * a2.y + ga * a4.y);
-        }
-      }
-      const long g = (long)k * inner + t0 + t;
-      if (MODE == kChebForwardT) {
-        if (real) reinterpret_cast<T*>(out)[g] = s.x; else reinterpret_cast<C*>(out)[g] = s;
-      } else {
-        to_spec<TS, C>(reinterpret_cast<TS*>(out), g, real, s);
-      }
-    }
+    cheb_forward_finish<T, MODE, TS, N>(buf, nt, t0, inner, basis, real, out, dctw);
   } else {  // backward
     staged_copy<N * TW, C>(
         [&](int idx) {
@@ -238,59 +322,12 @@ __global__ void __launch_bounds__(kFastThreads) k_cheb_fast(const void* __restri
           if (t < nt) buf[t * LDP + padi(k)] = v;
         });
     __syncthreads();
-    C a[PER];
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) {
-        const C* c = buf + t * LDP;
-        C v = c[padi(k)];
-        if (basis == kDirichlet) {
-          if (k >= 2) v = csub(v, c[padi(k - 2)]);
-        } else if (basis == kBiharmonic) {
-          if (k >= 2) { const T be = fbeta<T>(k - 2); const C u = c[padi(k - 2)]; v.x += be * u.x; v.y += be * u.y; }
-          if (k >= 4) { const T ga = fgamma<T>(k - 4); const C u = c[padi(k - 4)]; v.x += ga * u.x; v.y += ga * u.y; }
-        }
-        a[q] = v;
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) buf[t * LDP + padi(k)] = a[q];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) {
-        const C* c = buf + t * LDP;
-        if (k == 0) {
-          a[q] = c[padi(0)];
-        } else {
-          const C x = c[padi(k)], y = c[padi(N - k)];
-          const C d = mk<C>(x.x + y.y, x.y - y.x);
-          a[q] = cscale(cmulc(d, __ldg(&dctw[k])), (T)0.5);
-        }
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < PER; ++q) {
-      const int idx = threadIdx.x + q * kFastThreads;
-      const int t = idx / N, k = idx % N;
-      if (t < nt) buf[t * LDP + padi(k)] = a[q];
-    }
-    __syncthreads();
+    cheb_backward_prepare<T, N>(buf, nt, basis, dctw);
     fft_fast<N, TW, kFastThreads, true>(buf, nt, twf);
     for (int idx = threadIdx.x; idx < N * TW; idx += kFastThreads) {
       const int j = idx / TW, t = idx % TW;
       if (t < nt) {
-        const C v = buf[t * LDP + padi(reord(j))];
+        const C v = buf[t * LDP + padi(cheb_reord<N>(j))];
         const long g = (long)j * inner + t0 + t;
         if (real) reinterpret_cast<T*>(out)[g] = v.x; else reinterpret_cast<C*>(out)[g] = v;
       }

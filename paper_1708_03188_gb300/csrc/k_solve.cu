@@ -112,7 +112,7 @@ template <int NC> __device__ __forceinline__ void map_columns(const ColumnMap& m
 enum { TD_B0 = 0, TD_A0 = 1, TD_G = 2, TD_COUNT = 3 };
 enum { TB_B0 = 0, TB_B2, TB_B4, TB_ALO, TB_A0, TB_AUP, TB_S0, TB_S1, TB_S2, TB_G0, TB_G1, TB_F0, TB_F1, TB_COUNT };
 
-template <typename T, int NC>
+template <typename T, int NC, typename TO = T>
 __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict__ in, void* __restrict__ out, int N,
                                                          long ncols, int real, double a, double b,
                                                          const __grid_constant__ Wavenumbers wn,
@@ -211,6 +211,11 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
         for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
       }
       const double r = v[0], g = v[1];
+      // row i + 1 is stored one iteration late (see k_solve_biharmonic)
+      if (i + 1 < n) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) st2<TO>(out, off[q] + (long)(i + 1) * rstep, real, un[q]);
+      }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         Ts[q].x += un[q].x;
@@ -218,13 +223,139 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
         double2 u;
         u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
         u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
-        st2<T>(out, off[q] + (long)i * rstep, real, u);
         un[q] = u;
       }
     }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, off[q], real, un[q]);
+    }
     for (int k = nb + p; k < N; k += 2) {
 #pragma unroll
-      for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+      for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+    }
+  }
+}
+
+// Shen-Neumann, a lap(u) + b u = f (phi_k = T_k - q_k T_{k+2}, q_k = (k/(k+2))^2):
+// M = a A + aB B, aB = b - a kappa2.  Within a parity, with i the position (k = p + 2i):
+//   B: diagonal pi/2 (c_k + q_k^2), off-diagonals B_{k,k+2} = B_{k+2,k} = -pi/2 q_k;
+//   A: upper triangular, diagonal -2 pi k^2 (k+1)/(k+2), and A_{kj} = G_k F_j to the right of it
+//      with G_k = -4 pi (k+1)/(k+2)^2 and F_j = j^2 (a rank-one tail weighted by the trial index).
+//   Row i: l_i u_{i-1} + d_i u_i + e_i u_{i+1} + a G_k sum_{j >= i+2} F_j u_j,
+//   l_i = aB B_{k-2,k},  d_i = a A_kk + aB B_kk,  e_i = a G_k F_{k+2} + aB B_{k,k+2}.
+// Top-down elimination keeps that shape: mu = l_i / D_{i-1},  D_i = d_i - mu E_{i-1},
+// E_i = e_i - mu G'_{i-1} F_{k+2},  G'_i = a G_k - mu G'_{i-1},  f'_i = f_i - mu f'_{i-1};
+// back substitution u_i = (f'_i - E_i u_{i+1} - G'_i sum_{j >= i+2} F_j u_j) / D_i.
+// When aB = 0 (no zeroth-order term in this Fourier column) the constant phi_0 is in the null
+// space: the even parity then sets u_0 = 0 and drops the equation of phi_0, starting the
+// elimination at row 1.  Table layout (space.cu): TN_B0, TN_BUP (= B_{k,k+2}), TN_A0, TN_G.
+enum { TN_B0 = 0, TN_BUP = 1, TN_A0 = 2, TN_G = 3, TN_COUNT = 4 };
+
+template <typename T, int NC, typename TO = T>
+__global__ void __launch_bounds__(128) k_solve_neumann(const void* __restrict__ in, void* __restrict__ out, int N,
+                                                       long ncols, int real, double a, double b,
+                                                       const __grid_constant__ Wavenumbers wn,
+                                                       const __grid_constant__ ColumnMap cm,
+                                                       const double* __restrict__ tab, int ts,
+                                                       double* __restrict__ scratch) {
+  extern __shared__ double sh[];
+  double* tB0 = sh;
+  double* tBU = sh + ts;
+  double* aA0 = sh + 2 * ts;   // a * A_kk
+  double* aG = sh + 3 * ts;    // a * G_k
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    tB0[k] = tab[TN_B0 * ts + k];
+    tBU[k] = tab[TN_BUP * ts + k];
+    aA0[k] = a * tab[TN_A0 * ts + k];
+    aG[k] = a * tab[TN_G * ts + k];
+  }
+  __syncthreads();
+  constexpr int NV = 3 + 2 * NC;
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long nwb = (cm.nitems + 31) / 32;
+  const int nb = N - 2;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
+    const int p = (int)(w & 1);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
+    const double k2 = kappa2_of(wn, cc[0]);
+    const double aB = b - a * k2;
+    const int n = (nb - p + 1) / 2;
+    const int i0 = (p == 0 && aB == 0.0) ? 1 : 0;   // u_0 = 0 for the singular even parity
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    const long rstep = 2 * ncols;
+    double pr = 0.0, pE = 0.0, pG = 0.0;
+    double2 pf[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) pf[q] = make_double2(0.0, 0.0);
+    double* s = scratch + gt + (long)i0 * NV * nth;
+    const long sstep = (long)NV * nth;
+    for (int i = i0; i < n; ++i) {
+      const int k = p + 2 * i;
+      double2 f[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) f[q] = ld2<T>(in, off[q] + (long)i * rstep, real);
+      const double fk2 = (double)(k + 2) * (double)(k + 2);
+      double d = fma(aB, tB0[k], aA0[k]);
+      double e = fma(aB, tBU[k], aG[k] * fk2);
+      double g = aG[k];
+      if (i > i0) {
+        const double mu = aB * tBU[k - 2] * pr;
+        d = fma(-mu, pE, d);
+        e = fma(-mu * pG, fk2, e);
+        g = fma(-mu, pG, g);
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          f[q].x = fma(-mu, pf[q].x, f[q].x);
+          f[q].y = fma(-mu, pf[q].y, f[q].y);
+        }
+      }
+      const double r = rcp64(d);
+      s[0] = r;
+      s[nth] = e;
+      s[2 * nth] = g;
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        s[(3 + 2 * q) * nth] = f[q].x;
+        s[(4 + 2 * q) * nth] = f[q].y;
+        pf[q] = f[q];
+      }
+      s += sstep;
+      pr = r; pE = e; pG = g;
+    }
+    double2 un[NC], Ts[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { un[q] = make_double2(0.0, 0.0); Ts[q] = make_double2(0.0, 0.0); }
+    for (int i = n - 1; i >= i0; --i) {
+      const int k = p + 2 * i;
+      s -= sstep;
+      const double r = s[0], e = s[nth], g = s[2 * nth];
+      const double fk2 = (double)(k + 2) * (double)(k + 2);
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        double2 u;
+        u.x = fma(-g, Ts[q].x, fma(-e, un[q].x, s[(3 + 2 * q) * nth])) * r;
+        u.y = fma(-g, Ts[q].y, fma(-e, un[q].y, s[(4 + 2 * q) * nth])) * r;
+        st2<TO>(out, off[q] + (long)i * rstep, real, u);
+        // the tail seen by row i - 1 starts at row i + 1, the trial index k + 2
+        Ts[q].x = fma(fk2, un[q].x, Ts[q].x);
+        Ts[q].y = fma(fk2, un[q].y, Ts[q].y);
+        un[q] = u;
+      }
+    }
+    if (i0 == 1)
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, off[q], real, make_double2(0.0, 0.0));
+    for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
     }
   }
 }
@@ -244,7 +375,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
 //     u_{h-1} = (f'_{h-1} - ell a_h - g'_{h-1} A_h) / (d'_{h-1} + ell b_h + g'_{h-1} B_h),
 // after which side 0 back-substitutes rows h-2 .. 0 and side 1 forward-substitutes rows h .. n-1.
 // Each serial chain is half as long as in the one-sided kernel and twice as many warps run it.
-template <typename T, int NC>
+template <typename T, int NC, typename TO = T>
 __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict__ in, void* __restrict__ out, int N,
                                                           long ncols, int real, double a, double b,
                                                           const __grid_constant__ Wavenumbers wn,
@@ -400,7 +531,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
           // u_h = a_h + b_h u_{h-1},  T_h = A_h + B_h u_{h-1}
           un[q] = u;
           Ts[q] = make_double2(fma(Bh, u.x, Ah.x), fma(Bh, u.y, Ah.y));
-          if (valid) st2<T>(out, off[q] + (long)(h - 1) * rstep, real, u);
+          if (valid) st2<TO>(out, off[q] + (long)(h - 1) * rstep, real, u);
         }
       }
       // back substitution of rows h-2 .. 0 (Ts = T_{i+1} after adding u_{i+1})
@@ -427,14 +558,14 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
           double2 u;
           u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
           u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
-          if (valid) st2<T>(out, off[q] + (long)i * rstep, real, u);
+          if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
           un[q] = u;
         }
       }
       if (valid)
         for (int k = nb + p; k < N; k += 2) {
 #pragma unroll
-          for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+          for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
         }
     }
     __syncthreads();
@@ -454,7 +585,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
           double2 u;
           u.x = fma(bi, up[q].x, sr[(1 + 2 * q) * nth]);
           u.y = fma(bi, up[q].y, sr[(2 + 2 * q) * nth]);
-          if (valid) st2<T>(out, off[q] + (long)i * rstep, real, u);
+          if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
           up[q] = u;
         }
       }
@@ -463,7 +594,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
   }
 }
 
-template <typename T, int NC>
+template <typename T, int NC, typename TO = T>
 __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict__ in, void* __restrict__ out,
                                                           int N, long ncols, int real, double a, double b,
                                                           double cc0, const __grid_constant__ Wavenumbers wn,
@@ -603,6 +734,12 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
         for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
       }
       const double r = v[0], u1 = v[1], u2 = v[2], h0 = v[3], h1 = v[4];
+      // row i + 1 is stored one iteration late, so that its conversion to the output type
+      // does not hold up this row's dependent FP64 chain
+      if (i + 1 < n) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) st2<TO>(out, off[q] + (long)(i + 1) * rstep, real, ua[q]);
+      }
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         T0[q].x = fma(F0, uc[q].x, T0[q].x); T0[q].y = fma(F0, uc[q].y, T0[q].y);
@@ -610,21 +747,26 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
         double2 u;
         u.x = fma(-h1, T1[q].x, fma(-h0, T0[q].x, fma(-u2, ub[q].x, fma(-u1, ua[q].x, v[5 + 2 * q])))) * r;
         u.y = fma(-h1, T1[q].y, fma(-h0, T0[q].y, fma(-u2, ub[q].y, fma(-u1, ua[q].y, v[6 + 2 * q])))) * r;
-        st2<T>(out, off[q] + (long)i * rstep, real, u);
         uc[q] = ub[q]; ub[q] = ua[q]; ua[q] = u;
       }
     }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, off[q], real, ua[q]);
+    }
     for (int k = nb + p; k < N; k += 2) {
 #pragma unroll
-      for (int q = 0; q < NC; ++q) st2<T>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
+      for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
     }
   }
 }
 
 // Values per row per thread in the scratch for NC columns per thread.
-int solve_scratch_values(int basis, int nc) { return basis == kDirichlet ? 2 + 2 * nc : 5 + 2 * nc; }
+int solve_scratch_values(int basis, int nc) {
+  return basis == kDirichlet ? 2 + 2 * nc : basis == kNeumann ? 3 + 2 * nc : 5 + 2 * nc;
+}
 
-template <typename T, int NC>
+template <typename T, int NC, typename TO>
 static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
                             long ncols, const Wavenumbers& wn, const ColumnMap& cm, const double* tab, double* scratch,
                             long scratch_threads, cudaStream_t s) {
@@ -635,7 +777,18 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
   const unsigned grid = (unsigned)(threads / 128);
   const int ts = N + 8;
   cudaError_t e;
-  if (basis == kDirichlet && NC == 1) {
+  if (basis == kNeumann) {
+    if constexpr (NC <= 2) {
+      const size_t smem = sizeof(double) * 4 * ts;
+      if (smem > 48 * 1024 &&
+          (e = cudaFuncSetAttribute(k_solve_neumann<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+              cudaSuccess)
+        return e;
+      k_solve_neumann<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  } else if (basis == kDirichlet && NC == 1) {
     // two-sided kernel for the one-column-per-thread spaces (1-D and 2-D, few columns, long
     // serial chains); the 3-D box keeps the one-sided kernel, whose pairs already fill the GPU.
     // Four warps per 32 work items, each thread at most ceil(n / 2) rows of
@@ -649,27 +802,28 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
     const unsigned grid2 = (unsigned)std::max(1L, thr / 128);
     const size_t smem = sizeof(double) * (2 * ts + 2 * 32 * (6 * NC + 2));
     if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_solve_dirichlet2<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        (e = cudaFuncSetAttribute(k_solve_dirichlet2<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
             cudaSuccess)
       return e;
-    k_solve_dirichlet2<T, NC><<<grid2, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    k_solve_dirichlet2<T, NC, TO><<<grid2, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
   } else if (basis == kDirichlet) {
     const size_t smem = sizeof(double) * 2 * ts;
-    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    k_solve_dirichlet<T, NC><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    k_solve_dirichlet<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
   } else {
     const size_t smem = sizeof(double) * 13 * ts;
-    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    k_solve_biharmonic<T, NC><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
+    if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    k_solve_biharmonic<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
   }
   return cudaGetLastError();
 }
 
-// groups: device table of (a, b) for the four-column grouping, or nullptr
-template <typename T>
-cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
-                         long ncols, const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
-                         const int2* groups, long ngroups, cudaStream_t s) {
+// groups: device table of (a, b) for the four-column grouping, or nullptr; TO: type of the output
+// spectral data (T, or float for FP64 input whose solution is rounded once to FP32)
+template <typename T, typename TO>
+cudaError_t launch_solve_to(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
+                            long ncols, const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
+                            const int2* groups, long ngroups, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   ColumnMap cm;
   cm.pair_m1 = 0;
@@ -679,14 +833,29 @@ cudaError_t launch_solve(int basis, bool real, double a, double b, double c, con
   if (wn.n1 > 1 && groups) {
     cm.pair_m1 = wn.n1;
     cm.nitems = ngroups;
-    return solve_nc<T, 4>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+    return solve_nc<T, 4, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
   }
   if (wn.n1 > 1) {  // 3-D: pair +l1 / -l1 along axis 1
     cm.pair_m1 = wn.n1;
     cm.nitems = (1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0)) * (long)wn.n2;
-    return solve_nc<T, 2>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+    return solve_nc<T, 2, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
   }
-  return solve_nc<T, 1>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+  return solve_nc<T, 1, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
+}
+
+template <typename T>
+cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
+                         long ncols, const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
+                         const int2* groups, long ngroups, cudaStream_t s) {
+  return launch_solve_to<T, T>(basis, real, a, b, c, in, out, N, ncols, wn, tab, scratch, scratch_threads, groups,
+                               ngroups, s);
+}
+
+cudaError_t launch_solve_f64_to_f32(int basis, double a, double b, double c, const void* in, void* out, int N, long ncols,
+                                    const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
+                                    const int2* groups, long ngroups, cudaStream_t s) {
+  return launch_solve_to<double, float>(basis, false, a, b, c, in, out, N, ncols, wn, tab, scratch, scratch_threads,
+                                        groups, ngroups, s);
 }
 
 template cudaError_t launch_solve<float>(int, bool, double, double, double, const void*, void*, int, long,

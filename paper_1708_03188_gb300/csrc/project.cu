@@ -322,7 +322,7 @@ int upload_table(sgm_space* s, const std::vector<long double>& be, const std::ve
 // threads on consecutive columns.
 struct ShenStencil {
   int legendre;    // 1: Legendre weights 2/(2k+1)
-  int kind;        // kDirichlet or kBiharmonic (target basis)
+  int kind;        // kDirichlet, kNeumann or kBiharmonic (target basis)
 };
 
 __device__ __forceinline__ double series_weight(int legendre, int k) {
@@ -344,6 +344,8 @@ __global__ void __launch_bounds__(256) k_shen_scalar_of_series(const T* __restri
     double be, ga = 0.0;
     if (st.kind == kDirichlet) {
       be = -1.0;
+    } else if (st.kind == kNeumann) {
+      be = -neumann_q<double>(k);
     } else if (st.legendre) {
       be = -2.0 * (2 * k + 5) / (double)(2 * k + 7);
       ga = (double)(2 * k + 3) / (double)(2 * k + 7);
@@ -381,6 +383,9 @@ int build_project_table(sgm_space* s) {
   for (int j = 0; j < N; ++j) {
     if (s->kinds[0] == SGM_SHEN_DIRICHLET || s->kinds[0] == SGM_LEGENDRE_DIRICHLET) {
       be[j] = -1.0L;
+    } else if (s->kinds[0] == SGM_SHEN_NEUMANN) {
+      const long double r = (long double)j / (long double)(j + 2);
+      be[j] = -r * r;
     } else if (s->kinds[0] == SGM_SHEN_BIHARMONIC) {
       be[j] = -2.0L * (j + 2) / (long double)(j + 3);
       ga[j] = (long double)(j + 1) / (long double)(j + 3);
@@ -404,7 +409,8 @@ int project_regular(sgm_space* s, int axis, int order, const void* u_hat, void* 
   const int N = s->cheb ? (int)s->n[0] : 1;
   int nb = 1;
   if (s->cheb)
-    nb = (s->kinds[0] == SGM_SHEN_DIRICHLET || s->kinds[0] == SGM_LEGENDRE_DIRICHLET)       ? N - 2
+    nb = (s->kinds[0] == SGM_SHEN_DIRICHLET || s->kinds[0] == SGM_LEGENDRE_DIRICHLET ||
+          s->kinds[0] == SGM_SHEN_NEUMANN)                                                   ? N - 2
          : (s->kinds[0] == SGM_SHEN_BIHARMONIC || s->kinds[0] == SGM_LEGENDRE_BIHARMONIC) ? N - 4
                                                                                            : N;
   const long ncols = s->nspec / N;
@@ -443,7 +449,7 @@ int project_args(sgm_space* s, int axis, int order, const void* u_hat, const voi
   const char* a = (const char*)u_hat;
   const char* b = (const char*)du_hat;
   if (a < b + s->spec_bytes && b < a + s->spec_bytes) return set_error(SGM_ERR_ALIAS, "u_hat and du_hat overlap");
-  if (s->cheb && !s->pdx_tab) return set_error(SGM_ERR_STATE, "space has no derivative stencil table");
+  if (s->cheb && !s->inner && !s->pdx_tab) return set_error(SGM_ERR_STATE, "space has no derivative stencil table");
   return SGM_OK;
 }
 
@@ -457,6 +463,12 @@ bool is_legendre_kind(int kind) {
 extern "C" int sgm_project_dx(sgm_space* s, int axis, int order, const void* u_hat, void* du_hat, void* stream) {
   const int st = project_args(s, axis, order, u_hat, du_hat);
   if (st != SGM_OK) return st;
+  if (s->inner) {  // a permuted space (axes.cu): the canonical call on canonical copies
+    cudaStream_t cs = (cudaStream_t)stream;
+    PROJECT_TRY(to_canonical(s, SGM_SPECTRAL, u_hat, s->P1, cs));
+    PROJECT_TRY(sgm_project_dx(s->inner, s->perm[axis], order, s->P1, s->P2, stream));
+    return from_canonical(s, SGM_SPECTRAL, s->P2, du_hat, cs);
+  }
   return project_regular(s, axis, order, u_hat, du_hat, (cudaStream_t)stream);
 }
 
@@ -466,6 +478,16 @@ extern "C" int sgm_project(sgm_space* s, int axis, int order, const void* u_hat,
   if (st != SGM_OK) return st;
   st = space_check(target);
   if (st != SGM_OK) return st;
+  if (s->inner || target->inner) {  // permuted spaces (axes.cu): both in the same axis order
+    if (!s->inner || !target->inner || target->ndim != s->ndim)
+      return set_error(SGM_ERR_STATE, "target space has another axis order");
+    for (int d = 0; d < s->ndim; ++d)
+      if (target->perm[d] != s->perm[d]) return set_error(SGM_ERR_STATE, "target space has another axis order");
+    cudaStream_t cs = (cudaStream_t)stream;
+    PROJECT_TRY(to_canonical(s, SGM_SPECTRAL, u_hat, s->P1, cs));
+    PROJECT_TRY(sgm_project(s->inner, s->perm[axis], order, s->P1, target->inner, target->P2, stream));
+    return from_canonical(target, SGM_SPECTRAL, target->P2, out_hat, cs);
+  }
   if (target->ndim != s->ndim || target->prec != s->prec || target->cheb != s->cheb)
     return set_error(SGM_ERR_STATE, "target space differs in dimension, precision or axis-0 family");
   for (int d = 0; d < s->ndim; ++d) {
@@ -492,8 +514,10 @@ extern "C" int sgm_project(sgm_space* s, int axis, int order, const void* u_hat,
   const long ncols = s->nspec / N;
   const int tk = target->kinds[0];
   ShenStencil sst{target->legendre ? 1 : 0,
-                  (tk == SGM_SHEN_DIRICHLET || tk == SGM_LEGENDRE_DIRICHLET) ? (int)kDirichlet : (int)kBiharmonic};
-  const int nt = sst.kind == kDirichlet ? N - 2 : N - 4;
+                  (tk == SGM_SHEN_DIRICHLET || tk == SGM_LEGENDRE_DIRICHLET) ? (int)kDirichlet
+                  : tk == SGM_SHEN_NEUMANN                                   ? (int)kNeumann
+                                                                             : (int)kBiharmonic};
+  const int nt = basis_count(sst.kind, N);
   const long total = (long)N * ncols;
   const unsigned grid = (unsigned)((total + 255) / 256);
   const int R = s->real_spec ? 1 : 2;

@@ -180,7 +180,17 @@ int build_tables(sgm_space* s) {
   const int N = (int)s->n[0];
   const int ts = N + 8;
   std::vector<double> h;
-  if (s->kinds[0] == SGM_SHEN_DIRICHLET) {
+  if (s->kinds[0] == SGM_SHEN_NEUMANN) {
+    // TN_B0, TN_BUP, TN_A0, TN_G of k_solve_neumann (k_solve.cu)
+    h.assign(4 * ts, 0.0);
+    for (int k = 0; k < N - 2; ++k) {
+      const long double q = ((long double)k / (k + 2)) * ((long double)k / (k + 2));
+      h[0 * ts + k] = (double)(0.5L * kPi * ((k == 0 ? 2 : 1) + q * q));
+      h[1 * ts + k] = (double)(-0.5L * kPi * q);
+      h[2 * ts + k] = (double)(-2.0L * kPi * k * k * (k + 1) / (k + 2));
+      h[3 * ts + k] = (double)(-4.0L * kPi * (k + 1) / ((long double)(k + 2) * (k + 2)));
+    }
+  } else if (s->kinds[0] == SGM_SHEN_DIRICHLET) {
     h.assign(3 * ts, 0.0);
     for (int k = 0; k < N - 2; ++k) {
       h[0 * ts + k] = (double)(0.5L * kPi * ((k == 0 ? 2 : 1) + 1));
@@ -413,6 +423,7 @@ int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void
                                : legendre_solve<T>(s, a, b, c, in, out, wavenumbers(s), st);
   long ncols = 1;
   for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
+  if (s->kinds[0] == SGM_SHEN_NEUMANN) basis = kNeumann;
   return wrap(launch_solve<T>(basis, s->real_spec, a, b, c, in, out, (int)s->n[0], ncols, wavenumbers(s), s->tab,
                               s->scratch, s->scratch_threads, s->groups, s->ngroups, st),
               "solve");
@@ -432,7 +443,7 @@ template <typename T> int forward_impl(sgm_space* s, const void* u, void* out, c
   const int basis = s->kinds[0];
   if (basis == SGM_CHEBYSHEV || basis == SGM_LEGENDRE) return scalar_impl<T>(s, u, out, st, kChebForwardT);
   SGM_TRY(scalar_impl<T>(s, u, out, st, kChebScalar));
-  if (basis == SGM_SHEN_DIRICHLET || basis == SGM_LEGENDRE_DIRICHLET)
+  if (basis == SGM_SHEN_DIRICHLET || basis == SGM_LEGENDRE_DIRICHLET || basis == SGM_SHEN_NEUMANN)
     return solve_impl<T>(s, kDirichlet, 0.0, 1.0, 0.0, out, out, st);
   return solve_impl<T>(s, kBiharmonic, 0.0, 0.0, 1.0, out, out, st);
 }
@@ -453,7 +464,7 @@ int sgm::space_check(const sgm_space* s) { return check_space(s); }
 // with a Shen basis on axis 0, in place: B u = data.
 int sgm::space_mass_solve_f64(sgm_space* s, void* data, cudaStream_t st) {
   const int k = s->kinds[0];
-  if (k == SGM_SHEN_DIRICHLET || k == SGM_LEGENDRE_DIRICHLET)
+  if (k == SGM_SHEN_DIRICHLET || k == SGM_LEGENDRE_DIRICHLET || k == SGM_SHEN_NEUMANN)
     return solve_impl<double>(s, kDirichlet, 0.0, 1.0, 0.0, data, data, st);
   return solve_impl<double>(s, kBiharmonic, 0.0, 0.0, 1.0, data, data, st);
 }
@@ -461,6 +472,14 @@ int sgm::space_mass_solve_f64(sgm_space* s, void* data, cudaStream_t st) {
 namespace {
 
 void free_space(sgm_space* s) {
+  if (s->inner) {
+    sgm_space_destroy(s->inner);
+    cudaFree(s->P1);
+    cudaFree(s->P2);
+    s->magic = 0;
+    delete s;
+    return;
+  }
   for (auto& kv : s->tw) cudaFree(kv.second);
   s->tw.clear();
   for (auto& kv : s->twf) cudaFree(kv.second);
@@ -525,6 +544,15 @@ done:
 
 }  // namespace
 
+// one call on a permuted space (axes.cu): input of layout `win` -> P1 -> the canonical call
+// (P1 -> P2, or P1 in place) -> output of layout `wout`
+template <typename F>
+static int permuted_call(sgm_space* s, int win, const void* in, int wout, void* out, cudaStream_t st, F call) {
+  SGM_TRY(to_canonical(s, win, in, s->P1, st));
+  SGM_TRY(call(s->P1, s->P2));
+  return from_canonical(s, wout, s->P2, out, st);
+}
+
 extern "C" {
 
 const char* sgm_last_error(void) { return g_err.c_str(); }
@@ -549,25 +577,28 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   if (!out || !kinds || !n) return fail(SGM_ERR_NULL, "out, kinds and n must be non-NULL");
   *out = nullptr;
   if (ndim < 1 || ndim > 3) return fail(SGM_ERR_SIZE, "ndim must be 1..3 (got %d)", ndim);
+  if (!canonical_axes(ndim, kinds)) return permuted_create(out, ndim, kinds, n, domain, precision);
   const int cheb_flags = precision & (SGM_CHEB_TC | SGM_CHEB_AUTO);
   precision &= ~(SGM_CHEB_TC | SGM_CHEB_AUTO);
   if (precision != SGM_F32 && precision != SGM_F64) return fail(SGM_ERR_ARG, "precision must be SGM_F32 or SGM_F64");
   if (cheb_flags == (SGM_CHEB_TC | SGM_CHEB_AUTO)) return fail(SGM_ERR_ARG, "SGM_CHEB_TC and SGM_CHEB_AUTO exclude each other");
   if (cheb_flags && precision != SGM_F32) return fail(SGM_ERR_ARG, "Chebyshev-axis method flags need an SGM_F32 space");
   auto polynomial = [](int k) {
-    return k == SGM_CHEBYSHEV || k == SGM_SHEN_DIRICHLET || k == SGM_SHEN_BIHARMONIC || k == SGM_LEGENDRE ||
+    return k == SGM_CHEBYSHEV || k == SGM_SHEN_DIRICHLET || k == SGM_SHEN_BIHARMONIC || k == SGM_SHEN_NEUMANN ||
+           k == SGM_LEGENDRE ||
            k == SGM_LEGENDRE_DIRICHLET || k == SGM_LEGENDRE_BIHARMONIC;
   };
   const bool cheb = polynomial(kinds[0]);
   const bool legendre = kinds[0] == SGM_LEGENDRE || kinds[0] == SGM_LEGENDRE_DIRICHLET || kinds[0] == SGM_LEGENDRE_BIHARMONIC;
   for (int d = 0; d < ndim; ++d) {
     const int k = kinds[d];
-    if (k < SGM_CHEBYSHEV || k > SGM_LEGENDRE_BIHARMONIC) return fail(SGM_ERR_ARG, "axis %d: unknown basis kind %d", d, k);
+    if (k < SGM_CHEBYSHEV || k > SGM_SHEN_NEUMANN) return fail(SGM_ERR_ARG, "axis %d: unknown basis kind %d", d, k);
     if (d > 0 && polynomial(k)) return fail(SGM_ERR_SIZE, "axis %d: a Chebyshev or Legendre basis must be axis 0", d);
     if (k == SGM_FOURIER_R2C && d != ndim - 1) return fail(SGM_ERR_SIZE, "axis %d: only the last axis may be R2C", d);
     if (n[d] < 1 || n[d] > 4096) return fail(SGM_ERR_SIZE, "axis %d: size %lld outside 1..4096", d, (long long)n[d]);
   }
   if (kinds[0] == SGM_SHEN_DIRICHLET && n[0] < 4) return fail(SGM_ERR_SIZE, "Dirichlet basis needs N >= 4");
+  if (kinds[0] == SGM_SHEN_NEUMANN && n[0] < 4) return fail(SGM_ERR_SIZE, "Neumann basis needs N >= 4");
   if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] < 6) return fail(SGM_ERR_SIZE, "biharmonic basis needs N >= 6");
   // the biharmonic elimination stages 13 coefficient tables of N + 8 doubles in shared memory
   if (kinds[0] == SGM_SHEN_BIHARMONIC && n[0] > 2048)
@@ -623,10 +654,23 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   auto chk = [&](cudaError_t e, const char* what) {
     if (e != cudaSuccess && st == SGM_OK) st = fail(SGM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
   };
-  const size_t wbytes = std::max(s->spec_bytes, (size_t)s->nspec * s->celem());
+  // The streaming pipeline (k_stream.cu) of the physical-to-physical solves: FP32 spaces with a
+  // Shen Dirichlet or biharmonic axis 0 of a streaming length, its Chebyshev pass by the FFT, and
+  // Fourier axes C2C (axis 1 of a 3-D space) and R2C (last axis, even length) with streaming kernels.
+  if (cheb && !legendre && precision == SGM_F32 && !(cheb_flags && n[0] <= kTcMaxN) &&
+      (kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC || kinds[0] == SGM_SHEN_NEUMANN) &&
+      cheb_stream_length((int)n[0]) &&
+      kinds[ndim - 1] == SGM_FOURIER_R2C && n[ndim - 1] % 2 == 0 && rows_stream_length((int)(n[ndim - 1] / 2)) &&
+      (ndim == 2 || (ndim == 3 && kinds[1] == SGM_FOURIER_C2C && strided_stream_length((int)n[1])))) {
+    s->stream = true;
+    s->hp = (int)(n[ndim - 1] / 2 + 2);   // H + 1 coefficients rounded up to an even count
+    s->inner_p = (ndim == 3 ? n[1] : 1) * (long)s->hp;
+  }
+  const size_t npad = s->stream ? (size_t)n[0] * s->inner_p : 0;
+  const size_t wbytes = std::max({s->spec_bytes, (size_t)s->nspec * s->celem(), npad * s->celem()});
   chk(cudaMalloc(&s->W1, wbytes), "workspace");
   // W2 holds the spectral intermediate of the physical-to-physical solves, in FP64
-  chk(cudaMalloc(&s->W2, (size_t)s->nspec * 16), "workspace");
+  chk(cudaMalloc(&s->W2, std::max((size_t)s->nspec, npad) * 16), "workspace");
   if (st == SGM_OK && legendre) {
     st = legendre_build(s, cheb_flags != 0 && n[0] <= kTcMaxN);
     if (st == SGM_OK) st = build_project_table(s);
@@ -635,10 +679,11 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
     st = precision == SGM_F32 ? upload_dctw<float>(s, N) : upload_dctw<double>(s, N);
     if (st == SGM_OK) st = build_tables(s);
     if (st == SGM_OK) st = build_project_table(s);
-    if (st == SGM_OK && (kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC)) {
+    if (st == SGM_OK && (kinds[0] == SGM_SHEN_DIRICHLET || kinds[0] == SGM_SHEN_BIHARMONIC ||
+                         kinds[0] == SGM_SHEN_NEUMANN)) {
       int sms = 0;
       chk(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "device query");
-      long ncols = s->nspec / N;
+      long ncols = s->stream ? s->inner_p : s->nspec / N;
       long items = ncols;
       s->solve_nc = 1;
       if (ndim == 3) {
@@ -660,7 +705,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
           items = s->ngroups;
           s->solve_nc = 4;
         } else {
-          items = (1 + (n[1] - 1) / 2 + (n[1] % 2 == 0 ? 1 : 0)) * s->spec[2];
+          // the streaming pipeline solves its padded columns too (n2 = hp)
+          items = (1 + (n[1] - 1) / 2 + (n[1] % 2 == 0 ? 1 : 0)) * (s->stream ? (long)s->hp : s->spec[2]);
           s->solve_nc = 2;
         }
       }
@@ -668,7 +714,10 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       need = ((need + 127) / 128) * 128;
       s->scratch_threads = std::min((long)std::max(1, sms) * 256, need);
       const long rows = N / 2 + 1;
-      const int nv = solve_scratch_values(kinds[0] == SGM_SHEN_DIRICHLET ? kDirichlet : kBiharmonic, s->solve_nc);
+      const int nv = solve_scratch_values(kinds[0] == SGM_SHEN_DIRICHLET ? kDirichlet
+                                          : kinds[0] == SGM_SHEN_NEUMANN ? kNeumann
+                                                                         : kBiharmonic,
+                                          s->solve_nc);
       chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
     }
   }
@@ -685,6 +734,21 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
     if (st == SGM_OK) s->cheb_tc = (cheb_flags & SGM_CHEB_TC) ? 1 : autotune_cheb(s);
     if (s->cheb_tc < 0) st = SGM_ERR_CUDA;
   }
+  if (st == SGM_OK && s->stream) {
+    const uint64_t N0 = (uint64_t)n[0], ip = (uint64_t)s->inner_p;
+    const uint64_t dc[2] = {ip * 2, N0};
+    const uint32_t boxc[2] = {32, (uint32_t)N0};
+    const uint64_t sc1[1] = {ip * 8};
+    bool ok = encode_tiled_map(&s->map_w1, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, s->W1, dc, sc1, boxc) == cudaSuccess;
+    if (ok && ndim == 3) {
+      const uint64_t M1 = (uint64_t)n[1], hp = (uint64_t)s->hp;
+      const uint64_t ds[3] = {hp * 2, M1, N0};
+      const uint64_t ss[2] = {hp * 8, M1 * hp * 8};
+      const uint32_t boxs[3] = {32, (uint32_t)M1, 1};
+      ok = encode_tiled_map(&s->map_w1s, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, s->W1, ds, ss, boxs) == cudaSuccess;
+    }
+    if (!ok) st = fail(SGM_ERR_CUDA, "tensor map of the streaming pipeline rejected");
+  }
   if (st != SGM_OK) {
     free_space(s);
     return st;
@@ -696,15 +760,16 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
 int sgm_space_cheb_method(const sgm_space* space, int* method) {
   if (!space || !method) return fail(SGM_ERR_NULL, "NULL argument");
   if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  if (space->inner) return sgm_space_cheb_method(space->inner, method);
   *method = space->cheb_tc;
   return SGM_OK;
 }
 
 int sgm_tc_wait_timeouts(int* count, int reset) {
   if (!count) return fail(SGM_ERR_NULL, "NULL argument");
-  const int v = tc_timeouts(reset != 0), w = cnn_tc_timeouts(reset != 0);
-  if (v < 0 || w < 0) return fail(SGM_ERR_CUDA, "reading the device wait counters failed");
-  *count = v + w;
+  const int v = tc_timeouts(reset != 0), w = cnn_tc_timeouts(reset != 0), x = stream_timeouts(reset != 0);
+  if (v < 0 || w < 0 || x < 0) return fail(SGM_ERR_CUDA, "reading the device wait counters failed");
+  *count = v + w + x;
   return SGM_OK;
 }
 
@@ -726,6 +791,9 @@ int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out) {
 int sgm_scalar_product(sgm_space* s, const void* f, void* f_tilde, void* stream) {
   SGM_TRY(check_space(s));
   SGM_TRY(check_ptrs(f, s->phys_bytes, f_tilde, s->spec_bytes, false));
+  if (s->inner)
+    return permuted_call(s, SGM_PHYSICAL, f, SGM_SPECTRAL, f_tilde, (cudaStream_t)stream,
+                         [&](void* a, void* b) { return sgm_scalar_product(s->inner, a, b, stream); });
   cudaStream_t st = (cudaStream_t)stream;
   return s->prec == SGM_F32 ? scalar_impl<float>(s, f, f_tilde, st, kChebScalar)
                             : scalar_impl<double>(s, f, f_tilde, st, kChebScalar);
@@ -734,6 +802,9 @@ int sgm_scalar_product(sgm_space* s, const void* f, void* f_tilde, void* stream)
 int sgm_forward(sgm_space* s, const void* u, void* u_hat, void* stream) {
   SGM_TRY(check_space(s));
   SGM_TRY(check_ptrs(u, s->phys_bytes, u_hat, s->spec_bytes, false));
+  if (s->inner)
+    return permuted_call(s, SGM_PHYSICAL, u, SGM_SPECTRAL, u_hat, (cudaStream_t)stream,
+                         [&](void* a, void* b) { return sgm_forward(s->inner, a, b, stream); });
   cudaStream_t st = (cudaStream_t)stream;
   return s->prec == SGM_F32 ? forward_impl<float>(s, u, u_hat, st) : forward_impl<double>(s, u, u_hat, st);
 }
@@ -741,14 +812,17 @@ int sgm_forward(sgm_space* s, const void* u, void* u_hat, void* stream) {
 int sgm_backward(sgm_space* s, const void* u_hat, void* u, void* stream) {
   SGM_TRY(check_space(s));
   SGM_TRY(check_ptrs(u_hat, s->spec_bytes, u, s->phys_bytes, false));
+  if (s->inner)
+    return permuted_call(s, SGM_SPECTRAL, u_hat, SGM_PHYSICAL, u, (cudaStream_t)stream,
+                         [&](void* a, void* b) { return sgm_backward(s->inner, a, b, stream); });
   cudaStream_t st = (cudaStream_t)stream;
   return s->prec == SGM_F32 ? backward_impl<float>(s, u_hat, u, st) : backward_impl<double>(s, u_hat, u, st);
 }
 
 // the Helmholtz solver needs a Dirichlet basis, the biharmonic solver a biharmonic one (either family)
 static bool solver_matches(const sgm_space* s, int basis) {
-  const int k = s->kinds[0];
-  if (basis == kDirichlet) return k == SGM_SHEN_DIRICHLET || k == SGM_LEGENDRE_DIRICHLET;
+  const int k = s->inner ? s->inner->kinds[0] : s->kinds[0];
+  if (basis == kDirichlet) return k == SGM_SHEN_DIRICHLET || k == SGM_SHEN_NEUMANN || k == SGM_LEGENDRE_DIRICHLET;
   return k == SGM_SHEN_BIHARMONIC || k == SGM_LEGENDRE_BIHARMONIC;
 }
 
@@ -762,6 +836,10 @@ static int solve_entry(sgm_space* s, int basis, double a, double b, double c, co
     return fail(SGM_ERR_ARG, "a = b = c = 0 gives a singular system");
   SGM_TRY(check_ptrs(f, s->spec_bytes, u, s->spec_bytes, true));
   cudaStream_t st = (cudaStream_t)stream;
+  if (s->inner)
+    return permuted_call(s, SGM_SPECTRAL, f, SGM_SPECTRAL, u, st, [&](void* x, void* y) {
+      return solve_entry(s->inner, basis, a, b, c, x, y, stream);
+    });
   return s->prec == SGM_F32 ? solve_impl<float>(s, basis, a, b, c, f, u, st)
                             : solve_impl<double>(s, basis, a, b, c, f, u, st);
 }
@@ -773,6 +851,44 @@ int sgm_helmholtz_solve(sgm_space* s, double a, double b, const void* f_tilde, v
 int sgm_biharmonic_solve(sgm_space* s, double a, double b, double c, const void* f_tilde, void* u_hat,
                          void* stream) {
   return solve_entry(s, kBiharmonic, a, b, c, f_tilde, u_hat, stream);
+}
+
+// Physical -> physical on the streaming pipeline (FP32 spaces, see sgm_space::stream): R2C rows
+// into the padded W1, the strided C2C axis in place, the Chebyshev scalar product into the padded
+// FP64 W2, the FP64 solve from W2 with its result rounded once into W1 (the padding columns are
+// solved as dummy columns), and the Chebyshev, strided and C2R passes backwards from W1.
+static int stream_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u,
+                        cudaStream_t st) {
+  const int nd = s->ndim;
+  const int N0 = (int)s->n[0], M2 = (int)s->n[nd - 1], LF = M2 / 2;
+  const long nrows = nd == 3 ? s->n[0] * s->n[1] : s->n[0];
+  const void *twN = nullptr, *twLF = nullptr, *twM1 = nullptr;
+  SGM_TRY(need_twf(s, N0, &twN));
+  SGM_TRY(need_twf(s, LF, &twLF));
+  SGM_TRY(need_tw(s, M2));
+  if (nd == 3) SGM_TRY(need_twf(s, (int)s->n[1], &twM1));
+  const float2* twL = (const float2*)s->tw[M2];
+  float2* w1 = (float2*)s->W1;
+  SGM_TRY(wrap(launch_rows_stream(kRowR2C, LF, f, w1, nrows, s->hp, (const float2*)twLF, twL, st), "rows forward"));
+  if (nd == 3)
+    SGM_TRY(wrap(launch_strided_stream(false, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1, st),
+                 "strided forward"));
+  SGM_TRY(wrap(launch_cheb_stream(kChebScalar, N0, s->map_w1, s->W2, s->inner_p, s->kinds[0], (const float2*)twN,
+                                  (const float2*)s->dctw, st),
+               "chebyshev pass"));
+  Wavenumbers wn = wavenumbers(s);
+  wn.n2 = s->hp;
+  if (s->kinds[0] == SGM_SHEN_NEUMANN) basis = kNeumann;
+  SGM_TRY(wrap(launch_solve_f64_to_f32(basis, a, b, c, s->W2, w1, N0, s->inner_p, wn, s->tab, s->scratch,
+                                       s->scratch_threads, s->groups, s->ngroups, st),
+               "solve"));
+  SGM_TRY(wrap(launch_cheb_stream(kChebBackward, N0, s->map_w1, w1, s->inner_p, s->kinds[0], (const float2*)twN,
+                                  (const float2*)s->dctw, st),
+               "chebyshev pass"));
+  if (nd == 3)
+    SGM_TRY(wrap(launch_strided_stream(true, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1, st),
+                 "strided backward"));
+  return wrap(launch_rows_stream(kRowC2R, LF, w1, u, nrows, s->hp, (const float2*)twLF, twL, st), "rows backward");
 }
 
 // Physical -> physical: scalar product into W2 (FP64 spectral intermediate), FP64 solve in
@@ -788,6 +904,11 @@ static int full_entry(sgm_space* s, int basis, double a, double b, double c, con
     return fail(SGM_ERR_ARG, "a = b = c = 0 gives a singular system");
   SGM_TRY(check_ptrs(f, s->phys_bytes, u, s->phys_bytes, false));
   cudaStream_t st = (cudaStream_t)stream;
+  if (s->inner)
+    return permuted_call(s, SGM_PHYSICAL, f, SGM_PHYSICAL, u, st, [&](void* x, void* y) {
+      return full_entry(s->inner, basis, a, b, c, x, y, stream);
+    });
+  if (s->prec == SGM_F32 && s->stream) return stream_entry(s, basis, a, b, c, f, u, st);
   if (s->prec == SGM_F32) {
     SGM_TRY(scalar_impl<float>(s, f, s->W2, st, kChebScalar, true));
     SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));

@@ -1,6 +1,7 @@
 // space_internal.cuh - the sgm_space object shared by the host translation units
 // (space.cu, gl.cu).
 #pragma once
+#include <cuda.h>
 #include <map>
 #include <stdint.h>
 
@@ -41,6 +42,20 @@ struct sgm_space {
   double* leg_band = nullptr;   // band entries of the Legendre Galerkin matrices, 6 per basis row
   double* leg_scratch = nullptr;
   long leg_threads = 0;
+  // streaming pipeline of the physical-to-physical solves on FP32 spaces (k_stream.cu): W1
+  // (complex64) and W2 (FP64) hold the intermediates with the last axis padded to hp (even)
+  // coefficients per row, so every row starts on a 16-byte boundary; TMA tensor maps over W1 for
+  // the Chebyshev passes (as floats, 2-D) and the strided passes (3-D)
+  // a space whose axes are not in the canonical order (axes.cu) is a view of the canonical space
+  // `inner`: perm[d] = canonical axis of array axis d; P1, P2 = canonical-layout workspaces
+  sgm_space* inner = nullptr;
+  int perm[3] = {0, 1, 2};
+  void* P1 = nullptr;
+  void* P2 = nullptr;
+  bool stream = false;
+  int hp = 0;
+  long inner_p = 0;          // padded column count of the intermediates (M1 hp, or hp)
+  CUtensorMap map_w1, map_w1s;
 
   size_t celem() const { return prec == SGM_F32 ? 8 : 16; }
   size_t relem() const { return prec == SGM_F32 ? 4 : 8; }
@@ -51,6 +66,12 @@ namespace sgm {
 // precision (nullptr if L has no compiled kernel); owned by the space
 int need_twf(sgm_space* s, int L, const void** out);
 int space_check(const sgm_space* s);
+// spaces in another axis order (axes.cu): whether kinds are in the canonical order (polynomial
+// axis first, R2C axis last), the creation of a permuted view, and the layout permutations
+bool canonical_axes(int ndim, const int* kinds);
+int permuted_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n, const double* domain, int precision);
+int to_canonical(const sgm_space* s, int which, const void* in, void* out, cudaStream_t st);
+int from_canonical(const sgm_space* s, int which, const void* in, void* out, cudaStream_t st);
 // mass solve B u = data in place on FP64 spectral data of a space whose axis 0 is a Shen basis
 // (space.cu; uses the space's elimination scratch)
 int space_mass_solve_f64(sgm_space* s, void* data, cudaStream_t st);
@@ -66,6 +87,20 @@ int build_project_table(sgm_space* s);
 // (a Dirichlet problem a lap(u) + b u = f is (0, a, b): its tables have S = 0), on spectral data
 // of type TS (float or double)
 int legendre_build(sgm_space* s, bool tc_images);
+// streaming Chebyshev passes (k_stream.cu): lengths with a kernel, the launch (mode kChebScalar:
+// map over the complex64 intermediate, FP64 spectral out; kChebBackward: map over the FP64
+// spectral intermediate, complex64 out) and the tensor-map encoder (tma.cuh)
+bool cheb_stream_length(int N);
+cudaError_t launch_cheb_stream(int mode, int N, const CUtensorMap& map, void* out, long inner, int basis,
+                               const float2* twf, const float2* dctw, cudaStream_t s);
+bool rows_stream_length(int LF);
+bool strided_stream_length(int L);
+cudaError_t launch_rows_stream(int mode, int LF, const void* in, void* out, long nrows, int hp, const float2* twf,
+                               const float2* tw_L, cudaStream_t s);
+cudaError_t launch_strided_stream(bool inverse, int L, const CUtensorMap& map, float2* data, long outer, int hp,
+                                  const float2* twf, cudaStream_t s);
+cudaError_t encode_tiled_map(CUtensorMap* map, CUtensorMapDataType dtype, int rank, const void* base,
+                             const uint64_t* dims, const uint64_t* strides, const uint32_t* box);
 int legendre_pass(sgm_space* s, int mode, const void* in, void* out, cudaStream_t st, bool wide);
 template <typename TS>
 int legendre_solve(sgm_space* s, double a, double b, double c, const void* in, void* out, const Wavenumbers& wn,

@@ -49,7 +49,7 @@ def mesh(kinds, sizes, domains=None):
     out = []
     nd = len(sizes)
     for d, (k, n) in enumerate(zip(kinds, sizes)):
-        if k in ("chebyshev", "dirichlet", "biharmonic"):
+        if k in ("chebyshev", "dirichlet", "neumann", "biharmonic"):
             x = cheb_points(n)
         elif k in ("legendre", "legendre_dirichlet", "legendre_biharmonic"):
             x = legendre_points(n)
@@ -105,7 +105,7 @@ def coefficients(kinds, sizes, scale, workload="box3d", item=0, nvalid0=None, dt
         shp[-1] = sizes[-1] // 2 + 1
     knorm2 = np.zeros(shp)
     for d, (k, n) in enumerate(zip(kinds, sizes)):
-        if k in ("chebyshev", "dirichlet", "biharmonic"):
+        if k in ("chebyshev", "dirichlet", "neumann", "biharmonic"):
             idx = np.arange(n, dtype=np.float64)
         else:
             idx = signed_index(n, k == "r2c")

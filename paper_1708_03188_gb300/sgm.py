@@ -14,8 +14,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsgm.so")
 
 KINDS = {"chebyshev": 0, "dirichlet": 1, "biharmonic": 2, "c2c": 3, "r2c": 4,
-         "legendre": 5, "legendre_dirichlet": 6, "legendre_biharmonic": 7}
-POLYNOMIAL = ("chebyshev", "dirichlet", "biharmonic", "legendre", "legendre_dirichlet", "legendre_biharmonic")
+         "legendre": 5, "legendre_dirichlet": 6, "legendre_biharmonic": 7, "neumann": 8}
+POLYNOMIAL = ("chebyshev", "dirichlet", "biharmonic", "neumann", "legendre", "legendre_dirichlet",
+              "legendre_biharmonic")
 PRECISION = {"f32": 1, "f64": 2}
 CHEB_METHOD = {"fft": 0, "tc": 0x10, "auto": 0x20}
 _VP = ctypes.c_void_p
@@ -107,9 +108,10 @@ def _ptr(t):
 
 
 class Space:
-    """Tensor-product space (one Chebyshev or Legendre axis 0 + Fourier axes, or Fourier axes only).
+    """Tensor-product space (one Chebyshev or Legendre axis + Fourier axes, or Fourier axes only).
 
-    kinds: names from KINDS; sizes: quadrature points per axis; domain: [(lo, hi)] per
+    kinds: names from KINDS in the order of the array axes (the polynomial axis and the R2C axis
+    may sit on any axis: the axes option of Sec. 4); sizes: quadrature points per axis; domain: [(lo, hi)] per
     axis or None; precision "f32" (FP32 transforms, FP64 solves) or "f64"; cheb (f32 only):
     "fft" (DCT via FFT), "tc" (dense BF16x3 tensor-core contraction, N <= 128) or "auto"
     (the faster of the two, timed at creation).
@@ -132,8 +134,8 @@ class Space:
                                      PRECISION[precision] | CHEB_METHOD[cheb]))
         self.physical_shape = self._shape(0)
         self.spectral_shape = self._shape(1)
-        cheb = self.kinds[0] in POLYNOMIAL
-        self.real_physical = self.kinds[-1] == "r2c" or (cheb and nd == 1)
+        cheb = any(k in POLYNOMIAL for k in self.kinds)   # on any axis (the axes option of Sec. 4)
+        self.real_physical = "r2c" in self.kinds or (cheb and nd == 1)
         self.real_spectral = cheb and nd == 1
         rdt = torch.float32 if precision == "f32" else torch.float64
         cdt = torch.complex64 if precision == "f32" else torch.complex128
@@ -245,11 +247,8 @@ class Space:
         """W0: this space with axis 0 replaced by the regular basis of its family, Chebyshev or
         Legendre (a new Space with the same sizes, domain and precision); for a Fourier-only
         space, a copy of it."""
-        kinds = list(self.kinds)
-        if kinds[0] in ("dirichlet", "biharmonic"):
-            kinds[0] = "chebyshev"
-        elif kinds[0] in ("legendre_dirichlet", "legendre_biharmonic"):
-            kinds[0] = "legendre"
+        kinds = ["chebyshev" if k in ("dirichlet", "biharmonic", "neumann") else
+                 "legendre" if k in ("legendre_dirichlet", "legendre_biharmonic") else k for k in self.kinds]
         return Space(kinds, self.sizes, domain=self.domain, precision=self.precision)
 
 

@@ -47,8 +47,8 @@ def test_status_strings(libsgm):
 
 @pytest.mark.parametrize("ndim,kinds,sizes,code", [
     (0, [1], [8], -2),                 # ndim out of range
-    (2, [3, 1], [8, 8], -2),           # Chebyshev basis not on axis 0
-    (2, [4, 3], [8, 8], -2),           # R2C not on the last axis
+    (2, [1, 1], [8, 8], -2),           # two polynomial axes (any one axis may be polynomial)
+    (2, [4, 4], [8, 8], -2),           # two R2C axes (the R2C axis may be any one axis)
     (1, [1], [3], -2),                 # Dirichlet needs N >= 4
     (1, [2], [5], -2),                 # biharmonic needs N >= 6
     (1, [2], [2049], -2),              # biharmonic needs N <= 2048 (shared-memory tables)
