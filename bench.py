@@ -833,7 +833,7 @@ def closure_measure(stream, iters=1500):
             "coarse_plain_32": per_state_ms(closure.graphed(plain_step(coarse, states.clone())))}
     from paper_1708_03188_gb300.sgm import GinzburgLandau, Space
     matched = {}
-    for Mc in (64,):
+    for Mc in (40, 48, 64):
         snaps_m = closure.fine_trajectories(256, Mc, 2, 30.0, 20, 0.01, 0.05, first_item=100)
         cm = closure.CoarseModel(Mc, 0.05)
         start = snaps_m[:, :-1].reshape(-1, Mc, Mc)
@@ -852,7 +852,15 @@ def closure_measure(stream, iters=1500):
             for i in range(B):
                 glf.step(uf[i], 5)
         cost[f"fine_plain_256_{prec}"] = per_state_ms(closure.graphed(fine))
+    # cheapest plain grid whose one-step error reaches the learned one (the matched-accuracy
+    # comparison), and the statistics over 2000 coarse steps (t = 100) on held-out states
+    reach = [Mc for Mc in (40, 48, 64) if matched[f"plain_{Mc}"] <= e1l]
+    lh = closure.long_horizon(coarse, net, scale, nsteps=2000)
     return {"fine": "256^2, IF-RK4 dt 0.01", "coarse": "32^2, IF-RK4 dt 0.05", "params": net.num_params,
+            "matched_plain_grid": {"cheapest_plain_reaching_learned_one_step_error": reach[0] if reach else None,
+                                   "its_ms_per_state": round(cost[f"coarse_plain_{reach[0]}"], 5) if reach else None,
+                                   "learned_ms_per_state": round(cost["coarse_learned_32"], 5)},
+            "long_horizon": lh,
             "train": {"iters": iters, "batch": 32, "ms_per_iter": round(train_ms / iters, 4),
                       "loss_first_last": [round(hist[0], 4), round(hist[-1], 4)]},
             "one_step_rel_error": {"plain": e1p, "learned": e1l, **matched},

@@ -100,6 +100,7 @@ class CoarseModel:
 
     def __init__(self, M, dt, beta=1.5, gamma=-0.5, precision="f32"):
         self.M = M
+        self.dt = dt
         self.space = sgm.Space(["c2c", "c2c"], (M, M), domain=DOMAIN, precision=precision)
         self.gl = sgm.GinzburgLandau(self.space, beta, gamma, dt, "ifrk4")
 
@@ -242,3 +243,64 @@ def graphed(fn):
         fn()
     return g.replay
 
+
+
+def _energy_and_spectrum(uh, kbins):
+    """<|u|^2> (Parseval: the sum of |u_hat|^2 with the transform's 1/M^2) and the radial energy
+    spectrum (sum of |u_hat|^2 over the integer shells |k| in [s, s + 1)) of spectral states."""
+    e = uh.abs().pow(2)
+    energy = e.sum(dim=(1, 2))
+    spec = torch.zeros((uh.shape[0], int(kbins.max()) + 1), device=uh.device)
+    spec.index_add_(1, kbins.reshape(-1), e.reshape(uh.shape[0], -1).float())
+    return energy, spec
+
+
+def long_horizon(coarse, net, scale_t, Mf=256, nstates=4, nsteps=2000, t_spin=30.0, dt_f=0.01, first_item=200,
+                 beta=1.5, gamma=-0.5):
+    """Statistics over a long horizon (nsteps coarse steps of coarse.gl's dt) from held-out states:
+    the fine run (complex64 IF-RK4 on Mf^2 with dt_f), spectrally truncated to the coarse grid every
+    coarse step, against the plain coarse run and the corrected one.  The flow is chaotic, so the
+    trajectories decorrelate; what a closure can get right is the statistics.  Returns the relative
+    errors of the time-averaged <|u|^2> and of the time-averaged radial energy spectrum over the
+    second half of the horizon, for the plain and the learned coarse runs."""
+    Mc = coarse.M
+    dt_c = coarse.dt
+    sp = sgm.Space(["c2c", "c2c"], (Mf, Mf), domain=DOMAIN, precision="f32")
+    gl = sgm.GinzburgLandau(sp, beta, gamma, dt_f, "ifrk4")
+    per = int(round(dt_c / dt_f))
+    fine = [sp.forward(torch.from_numpy(inputs.gl_initial(Mf, first_item + s)).to(torch.complex64).cuda())
+            for s in range(nstates)]
+    for uh in fine:
+        gl.step(uh, int(round(t_spin / dt_f)))
+    start = torch.empty((nstates, Mc, Mc), dtype=torch.complex64, device="cuda")
+    for s, uh in enumerate(fine):
+        sgm.spectral_truncate(uh.unsqueeze(0), start[s].unsqueeze(0))
+    l = torch.from_numpy(np.fft.fftfreq(Mc, 1.0 / Mc)).cuda()
+    kbins = torch.sqrt(l[:, None] ** 2 + l[None, :] ** 2).floor().long()
+    plain, learned = start.clone(), start.clone()
+    acc = {name: [0.0, 0.0] for name in ("fine", "plain", "learned")}
+    trunc = torch.empty_like(start)
+    half = nsteps // 2
+    for n in range(1, nsteps + 1):
+        for s, uh in enumerate(fine):
+            gl.step(uh, per)
+            sgm.spectral_truncate(uh.unsqueeze(0), trunc[s].unsqueeze(0))
+        plain = coarse.step_batch(plain)
+        learned = corrected_step(coarse, net, learned, scale_t)
+        if n > half:
+            for name, st in (("fine", trunc), ("plain", plain), ("learned", learned)):
+                e, spec = _energy_and_spectrum(st, kbins)
+                acc[name][0] = acc[name][0] + e.mean()
+                acc[name][1] = acc[name][1] + spec.mean(dim=0)
+    gl.close()
+    sp.close()
+    ef, sf = acc["fine"]
+    out = {"horizon_steps": nsteps, "time_units": round(nsteps * dt_c, 3), "states": nstates,
+           "averaged_over": "second half of the horizon"}
+    for name in ("plain", "learned"):
+        e, spec = acc[name]
+        out[name] = {"energy_rel_error": float(abs(e - ef) / ef),
+                     "spectrum_rel_l2": float(torch.linalg.vector_norm(spec - sf) / torch.linalg.vector_norm(sf)),
+                     "finite": bool(torch.isfinite(e).item())}
+    out["fine_energy"] = float(ef / (nsteps - half))
+    return out

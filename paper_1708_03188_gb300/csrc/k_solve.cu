@@ -41,7 +41,7 @@
 // Coefficient tables are pre-multiplied by the call's scalars into shared memory.
 // Each sweep loads the next row's operands one row ahead, so the global-memory latency
 // overlaps the FP64 work of the current row.
-// Reciprocals: the PTX approximate FP64 reciprocal refined by one third-order Newton step
+// Reciprocals: the PTX approximate FP64 reciprocal refined by one step of a third-order iteration
 // (r <- r + r (e + e^2), e = 1 - x r), which cubes the relative error.  FP32 data is
 // widened and narrowed on the integer pipe (convert.cuh).
 #include <algorithm>
@@ -52,8 +52,10 @@
 namespace sgm {
 
 __device__ __forceinline__ double rcp64(double x) {
-  // seed: PTX rcp.approx.ftz.f64 (relative error below 2^-22 for normal x); one cubic
-  // Newton step r (1 + e + e^2), e = 1 - x r, takes the error to its cube (< 2^-66).
+  // seed: PTX rcp.approx.ftz.f64 (relative error below 2^-22 for normal x); one step of the
+  // third-order (Householder's order-2, or Chebyshev's) iteration for 1/x, r (1 + e + e^2) with
+  // e = 1 - x r: since 1/x = r / (1 - e) = r (1 + e + e^2 + ...), the truncation leaves a relative
+  // error e^3, the cube of the seed's (< 2^-66).
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
   const double e = fma(-x, r, 1.0);
