@@ -145,6 +145,14 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
 int sgm_space_destroy(sgm_space* space);
 /* Write the ndim extents of the PHYSICAL or SPECTRAL array into shape_out. */
 int sgm_space_shape(const sgm_space* space, int which, int64_t* shape_out);
+/*
+ * Measurement hook (no counterpart in the paper): events (cudaEvent_t passed as void*, owned by the
+ * caller) that the physical-to-physical solves of this space (sgm_helmholtz, sgm_biharmonic) record
+ * on the caller's stream right before and right after their elimination kernel, so that a caller
+ * can time that kernel inside a longer sequence of work.  Both NULL clears them; one NULL is
+ * SGM_ERR_ARG.  The events are recorded by every later solve until cleared.
+ */
+int sgm_space_solve_events(sgm_space* space, void* begin, void* end);
 /* Chebyshev-axis method in use: *method = 0 (DCT via FFT), 1 (tensor-core contraction). */
 int sgm_space_cheb_method(const sgm_space* space, int* method);
 /*

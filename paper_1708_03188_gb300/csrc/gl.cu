@@ -66,15 +66,15 @@ template <typename T> int upload_E(sgm_gl* g) {
   return SGM_OK;
 }
 
-template <typename T> int launch(sgm_gl* g, int mode, const void* Vin, void* Vout, void* S, void* out, int stage,
-                                 cudaStream_t st) {
+template <typename T> int launch(sgm_gl* g, int mode, bool pad_first, bool pad_next, const void* Vin, void* Vout,
+                                 void* S, void* out, int stage, cudaStream_t st) {
   GlParams prm;
   prm.beta = g->beta;
   prm.gamma = g->gamma;
   prm.dt = g->dt;
   prm.kscale = 2.0 * 3.141592653589793 / g->length;
   prm.stage = stage;
-  cudaError_t e = gl_launch<T>(g->M, mode, (const cplx<T>*)Vin, (cplx<T>*)Vout, (cplx<T>*)g->A, (cplx<T>*)S,
+  cudaError_t e = gl_launch<T>(g->M, mode, pad_first, pad_next, (const cplx<T>*)Vin, (cplx<T>*)Vout, (cplx<T>*)g->A, (cplx<T>*)S,
                                (const cplx<T>*)g->E, (cplx<T>*)out, (cplx<T>*)g->P, prm, (const cplx<T>*)g->twf, st);
   if (e != cudaSuccess) return set_error(SGM_ERR_CUDA, "Ginzburg-Landau launch: %s", cudaGetErrorString(e));
   return SGM_OK;
@@ -82,9 +82,13 @@ template <typename T> int launch(sgm_gl* g, int mode, const void* Vin, void* Vou
 
 template <typename T> int step_impl(sgm_gl* g, void* u, int nsteps, cudaStream_t st) {
   const int mode = g->scheme == SGM_GL_IFRK4 ? kGlIfRk4 : kGlRk4;
+  // one run of 4 * nsteps stages: only the first pads its input itself; every stage but the last
+  // leaves the padded, back-transformed input of the next stage in P
+  const long total = 4L * nsteps;
+  long i = 0;
   for (int n = 0; n < nsteps; ++n)
-    for (int s = 0; s < 4; ++s) {
-      int r = launch<T>(g, mode, s == 0 ? u : g->V, g->V, u, nullptr, s, st);
+    for (int s = 0; s < 4; ++s, ++i) {
+      int r = launch<T>(g, mode, i == 0, i + 1 < total, s == 0 ? u : g->V, g->V, u, nullptr, s, st);
       if (r != SGM_OK) return r;
     }
   return SGM_OK;
@@ -158,8 +162,8 @@ int sgm_gl_rhs(sgm_gl* gl, const void* u_hat, void* rhs, void* stream) {
   const char* b = (const char*)rhs;
   if (a < b + bytes && b < a + bytes) return set_error(SGM_ERR_ALIAS, "u_hat and rhs overlap");
   cudaStream_t s = (cudaStream_t)stream;
-  return gl->prec == SGM_F32 ? launch<float>(gl, kGlRhs, u_hat, nullptr, nullptr, rhs, 0, s)
-                             : launch<double>(gl, kGlRhs, u_hat, nullptr, nullptr, rhs, 0, s);
+  return gl->prec == SGM_F32 ? launch<float>(gl, kGlRhs, true, false, u_hat, nullptr, nullptr, rhs, 0, s)
+                             : launch<double>(gl, kGlRhs, true, false, u_hat, nullptr, nullptr, rhs, 0, s);
 }
 
 int sgm_gl_step(sgm_gl* gl, void* u_hat, int nsteps, void* stream) {

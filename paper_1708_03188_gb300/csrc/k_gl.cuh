@@ -18,7 +18,11 @@
 //   K3 k_gl_rows_out   each row of P: forward FFT (x 1/Mp), truncate to M, then either write
 //                      the right-hand side or apply one RK4 stage update (explicit RK4 of the
 //                      paper's time loop, or integrating-factor RK4) to the stage input V,
-//                      the accumulator A and the state S.
+//                      the accumulator A and the state S.  Within a run of stages K3 also does
+//                      the next stage's K1 on the rows it holds (PAD_NEXT): the rows of the new
+//                      stage input (or, after the last stage, of the new state) are already in
+//                      its shared memory, so it zero-pads them, transforms them back and writes
+//                      them to P, and a stage costs two launches instead of three.
 // Explicit RK4 (a = 1/6, 1/3, 1/3, 1/6; b = 1/2, 1/2, 1), stage s with input V (V = S at s = 0):
 //     d = L V - N(V);  s < 3: V <- S + b_s dt d, A <- (s ? A : S) + a_s dt d;  s = 3: S <- A + a_3 dt d.
 // Integrating-factor RK4 (classical RK4 on exp(-L t) u_hat, E = exp(L dt / 2)), n = -N(V):
@@ -122,8 +126,8 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_cols(cplx<T>* __restrict__ 
   }
 }
 
-template <typename T, int M, int MP, int MODE>
-__global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __restrict__ P, const cplx<T>* Vin,
+template <typename T, int M, int MP, int MODE, bool PAD_NEXT>
+__global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(cplx<T>* __restrict__ P, const cplx<T>* Vin,
                                                               cplx<T>* Vout, cplx<T>* A, cplx<T>* S,
                                                               const cplx<T>* __restrict__ E, cplx<T>* out,
                                                               const __grid_constant__ GlParams prm,
@@ -146,7 +150,9 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
     const int line = idx / M, j = idx - line * M;
     const int r = r0 + line;
     const long g = (long)r * M + j;
-    const C nl_ = cscale(buf[line * LDP + padi(gl_padpos<M, MP>(j))], inv);   // N(V) at (r, j)
+    C* slot = &buf[line * LDP + padi(gl_padpos<M, MP>(j))];   // read and rewritten by this thread only
+    const C nl_ = cscale(*slot, inv);                          // N(V) at (r, j)
+    C nv = mk<C>((T)0, (T)0);                                  // next stage input (or new state) at (r, j)
     if (MODE == kGlIfRk4) {
       const C n = mk<C>(-nl_.x, -nl_.y);
       const C e = E[g];
@@ -154,14 +160,16 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
       switch (prm.stage) {
         case 0: {
           const C e2 = cmul(e, e);
-          Vout[g] = cmul(e, mk<C>(s.x + (T)0.5 * dt * n.x, s.y + (T)0.5 * dt * n.y));
+          nv = cmul(e, mk<C>(s.x + (T)0.5 * dt * n.x, s.y + (T)0.5 * dt * n.y));
+          Vout[g] = nv;
           const C t = cadd(s, cscale(n, dt / (T)6));
           A[g] = cmul(e2, t);
           break;
         }
         case 1: {
           const C es = cmul(e, s);
-          Vout[g] = mk<C>(es.x + (T)0.5 * dt * n.x, es.y + (T)0.5 * dt * n.y);
+          nv = mk<C>(es.x + (T)0.5 * dt * n.x, es.y + (T)0.5 * dt * n.y);
+          Vout[g] = nv;
           const C en = cmul(e, n);
           const C a = A[g];
           A[g] = mk<C>(a.x + dt / (T)3 * en.x, a.y + dt / (T)3 * en.y);
@@ -171,14 +179,16 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
           const C e2 = cmul(e, e);
           const C en = cmul(e, n);
           const C e2s = cmul(e2, s);
-          Vout[g] = mk<C>(e2s.x + dt * en.x, e2s.y + dt * en.y);
+          nv = mk<C>(e2s.x + dt * en.x, e2s.y + dt * en.y);
+          Vout[g] = nv;
           const C a = A[g];
           A[g] = mk<C>(a.x + dt / (T)3 * en.x, a.y + dt / (T)3 * en.y);
           break;
         }
         default: {
           const C a = A[g];
-          S[g] = mk<C>(a.x + dt / (T)6 * n.x, a.y + dt / (T)6 * n.y);
+          nv = mk<C>(a.x + dt / (T)6 * n.x, a.y + dt / (T)6 * n.y);
+          S[g] = nv;
           break;
         }
       }
@@ -198,20 +208,57 @@ __global__ void __launch_bounds__(kFastThreads) k_gl_rows_out(const cplx<T>* __r
           const C s = S[g];
           const C base = (st == 0) ? s : A[g];
           A[g] = mk<C>(base.x + a_s * dt * d.x, base.y + a_s * dt * d.y);
-          Vout[g] = mk<C>(s.x + b_s * dt * d.x, s.y + b_s * dt * d.y);
+          nv = mk<C>(s.x + b_s * dt * d.x, s.y + b_s * dt * d.y);
+          Vout[g] = nv;
         } else {
           const C a = A[g];
-          S[g] = mk<C>(a.x + a_s * dt * d.x, a.y + a_s * dt * d.y);
+          nv = mk<C>(a.x + a_s * dt * d.x, a.y + a_s * dt * d.y);
+          S[g] = nv;
         }
       }
+    }
+    if constexpr (PAD_NEXT) *slot = nv;
+  }
+  if constexpr (PAD_NEXT) {
+    // the next stage's K1 on these rows: the padded positions that hold no original wavenumber
+    // (read by no thread above) become zero, then the rows are transformed back into P
+    constexpr int NZ = MP - M;
+    for (int idx = threadIdx.x; idx < nl * NZ; idx += kFastThreads) {
+      const int line = idx / NZ, q = (M + 1) / 2 + (idx - line * NZ);
+      buf[line * LDP + padi(q)] = mk<C>((T)0, (T)0);
+    }
+    __syncthreads();
+    fft_fast<MP, LINES, kFastThreads, true>(buf, nl, twf);
+    for (int idx = threadIdx.x; idx < nl * MP; idx += kFastThreads) {
+      const int line = idx / MP, q = idx - line * MP;
+      P[(long)(r0 + line) * MP + q] = buf[line * LDP + padi(q)];
     }
   }
 }
 
 // ---- launch of one right-hand side evaluation + stage update --------------------------------
+// pad_first: run K1 on Vin (otherwise P already holds the padded, back-transformed rows of Vin,
+// written by the previous launch with pad_next); pad_next: K3 also prepares P for the next stage
+// from the stage's result (the new V, or S after stage 3).
+template <typename T, int M, int MP, int MODE>
+cudaError_t gl_rows_out(bool pad_next, unsigned grid, size_t smem, cplx<T>* P, const cplx<T>* Vin,
+                        cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E, cplx<T>* out, const GlParams& prm,
+                        const cplx<T>* twf, cudaStream_t st) {
+  cudaError_t e;
+  if (pad_next) {
+    if ((e = fast_smem(k_gl_rows_out<T, M, MP, MODE, true>, smem)) != cudaSuccess) return e;
+    k_gl_rows_out<T, M, MP, MODE, true><<<grid, kFastThreads, smem, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+  } else {
+    if ((e = fast_smem(k_gl_rows_out<T, M, MP, MODE, false>, smem)) != cudaSuccess) return e;
+    k_gl_rows_out<T, M, MP, MODE, false><<<grid, kFastThreads, smem, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+  }
+  return cudaSuccess;
+}
+
 template <typename T, int M, int MP>
-cudaError_t gl_launch_sized(int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E,
-                            cplx<T>* out, cplx<T>* P, const GlParams& prm, const cplx<T>* twf, cudaStream_t st) {
+cudaError_t gl_launch_sized(int mode, bool pad_first, bool pad_next, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A,
+                            cplx<T>* S, const cplx<T>* E, cplx<T>* out, cplx<T>* P, const GlParams& prm,
+                            const cplx<T>* twf, cudaStream_t st) {
   constexpr int LINES = gl_lines<T, M, MP>();
   constexpr int TW = gl_tw<T, MP>();
   const size_t smem_rows = sizeof(cplx<T>) * LINES * pad_ld(MP);
@@ -220,30 +267,31 @@ cudaError_t gl_launch_sized(int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>
   if ((e = fast_smem(k_gl_rows_pad<T, M, MP>, smem_rows)) != cudaSuccess) return e;
   if ((e = fast_smem(k_gl_cols<T, M, MP>, smem_cols)) != cudaSuccess) return e;
   const unsigned grows = (M + LINES - 1) / LINES;
-  k_gl_rows_pad<T, M, MP><<<grows, kFastThreads, smem_rows, st>>>(Vin, P, twf);
+  if (pad_first) k_gl_rows_pad<T, M, MP><<<grows, kFastThreads, smem_rows, st>>>(Vin, P, twf);
   k_gl_cols<T, M, MP><<<(MP + TW - 1) / TW, kFastThreads, smem_cols, st>>>(P, twf, prm.gamma);
   switch (mode) {
     case kGlRhs:
-      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlRhs>, smem_rows)) != cudaSuccess) return e;
-      k_gl_rows_out<T, M, MP, kGlRhs><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      e = gl_rows_out<T, M, MP, kGlRhs>(false, grows, smem_rows, P, Vin, Vout, A, S, E, out, prm, twf, st);
       break;
     case kGlRk4:
-      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlRk4>, smem_rows)) != cudaSuccess) return e;
-      k_gl_rows_out<T, M, MP, kGlRk4><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      e = gl_rows_out<T, M, MP, kGlRk4>(pad_next, grows, smem_rows, P, Vin, Vout, A, S, E, out, prm, twf, st);
       break;
     default:
-      if ((e = fast_smem(k_gl_rows_out<T, M, MP, kGlIfRk4>, smem_rows)) != cudaSuccess) return e;
-      k_gl_rows_out<T, M, MP, kGlIfRk4><<<grows, kFastThreads, smem_rows, st>>>(P, Vin, Vout, A, S, E, out, prm, twf);
+      e = gl_rows_out<T, M, MP, kGlIfRk4>(pad_next, grows, smem_rows, P, Vin, Vout, A, S, E, out, prm, twf, st);
       break;
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t gl_launch(int M, int mode, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A, cplx<T>* S, const cplx<T>* E,
-                      cplx<T>* out, cplx<T>* P, const GlParams& prm, const cplx<T>* twf, cudaStream_t st) {
+cudaError_t gl_launch(int M, int mode, bool pad_first, bool pad_next, const cplx<T>* Vin, cplx<T>* Vout, cplx<T>* A,
+                      cplx<T>* S, const cplx<T>* E, cplx<T>* out, cplx<T>* P, const GlParams& prm,
+                      const cplx<T>* twf, cudaStream_t st) {
   switch (M) {
-#define SGM_GL(m) case m: return gl_launch_sized<T, m, 3 * m / 2>(mode, Vin, Vout, A, S, E, out, P, prm, twf, st);
+#define SGM_GL(m)                                                                                                \
+  case m:                                                                                                        \
+    return gl_launch_sized<T, m, 3 * m / 2>(mode, pad_first, pad_next, Vin, Vout, A, S, E, out, P, prm, twf, st);
     SGM_GL(32) SGM_GL(64) SGM_GL(128) SGM_GL(256) SGM_GL(512) SGM_GL(1024)
 #undef SGM_GL
     default: return cudaErrorInvalidValue;

@@ -2,6 +2,6 @@
 #include "k_gl.cuh"
 
 namespace sgm {
-template cudaError_t gl_launch<double>(int, int, const double2*, double2*, double2*, double2*, const double2*, double2*, double2*, const GlParams&,
+template cudaError_t gl_launch<double>(int, int, bool, bool, const double2*, double2*, double2*, double2*, const double2*, double2*, double2*, const GlParams&,
                                    const double2*, cudaStream_t);
 }  // namespace sgm

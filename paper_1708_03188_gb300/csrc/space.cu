@@ -757,6 +757,16 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   return SGM_OK;
 }
 
+int sgm_space_solve_events(sgm_space* space, void* begin, void* end) {
+  if (!space) return fail(SGM_ERR_NULL, "NULL space");
+  if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
+  if ((begin == nullptr) != (end == nullptr)) return fail(SGM_ERR_ARG, "give both events or neither");
+  if (space->inner) return sgm_space_solve_events(space->inner, begin, end);
+  space->ev_solve_begin = (cudaEvent_t)begin;
+  space->ev_solve_end = (cudaEvent_t)end;
+  return SGM_OK;
+}
+
 int sgm_space_cheb_method(const sgm_space* space, int* method) {
   if (!space || !method) return fail(SGM_ERR_NULL, "NULL argument");
   if (space->magic != sgm_space::kMagic) return fail(SGM_ERR_STATE, "not a live sgm_space");
@@ -869,9 +879,11 @@ static int stream_entry(sgm_space* s, int basis, double a, double b, double c, c
   if (nd == 3) SGM_TRY(need_twf(s, (int)s->n[1], &twM1));
   const float2* twL = (const float2*)s->tw[M2];
   float2* w1 = (float2*)s->W1;
-  SGM_TRY(wrap(launch_rows_stream(kRowR2C, LF, f, w1, nrows, s->hp, (const float2*)twLF, twL, st), "rows forward"));
+  SGM_TRY(wrap(launch_rows_stream(kRowR2C, LF, f, w1, nrows, s->hp, (const float2*)twLF, twL, st),
+               "rows forward"));
   if (nd == 3)
-    SGM_TRY(wrap(launch_strided_stream(false, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1, st),
+    SGM_TRY(wrap(launch_strided_stream(false, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1,
+                                       st),
                  "strided forward"));
   SGM_TRY(wrap(launch_cheb_stream(kChebScalar, N0, s->map_w1, s->W2, s->inner_p, s->kinds[0], (const float2*)twN,
                                   (const float2*)s->dctw, st),
@@ -879,16 +891,20 @@ static int stream_entry(sgm_space* s, int basis, double a, double b, double c, c
   Wavenumbers wn = wavenumbers(s);
   wn.n2 = s->hp;
   if (s->kinds[0] == SGM_SHEN_NEUMANN) basis = kNeumann;
+  if (s->ev_solve_begin) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_begin, st), "solve event"));
   SGM_TRY(wrap(launch_solve_f64_to_f32(basis, a, b, c, s->W2, w1, N0, s->inner_p, wn, s->tab, s->scratch,
                                        s->scratch_threads, s->groups, s->ngroups, st),
                "solve"));
+  if (s->ev_solve_end) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_end, st), "solve event"));
   SGM_TRY(wrap(launch_cheb_stream(kChebBackward, N0, s->map_w1, w1, s->inner_p, s->kinds[0], (const float2*)twN,
                                   (const float2*)s->dctw, st),
                "chebyshev pass"));
   if (nd == 3)
-    SGM_TRY(wrap(launch_strided_stream(true, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1, st),
+    SGM_TRY(wrap(launch_strided_stream(true, (int)s->n[1], s->map_w1s, w1, s->n[0], s->hp, (const float2*)twM1,
+                                       st),
                  "strided backward"));
-  return wrap(launch_rows_stream(kRowC2R, LF, w1, u, nrows, s->hp, (const float2*)twLF, twL, st), "rows backward");
+  return wrap(launch_rows_stream(kRowC2R, LF, w1, u, nrows, s->hp, (const float2*)twLF, twL, st),
+              "rows backward");
 }
 
 // Physical -> physical: scalar product into W2 (FP64 spectral intermediate), FP64 solve in
@@ -909,13 +925,19 @@ static int full_entry(sgm_space* s, int basis, double a, double b, double c, con
       return full_entry(s->inner, basis, a, b, c, x, y, stream);
     });
   if (s->prec == SGM_F32 && s->stream) return stream_entry(s, basis, a, b, c, f, u, st);
+  auto solve = [&]() -> int {
+    if (s->ev_solve_begin) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_begin, st), "solve event"));
+    SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));
+    if (s->ev_solve_end) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_end, st), "solve event"));
+    return SGM_OK;
+  };
   if (s->prec == SGM_F32) {
     SGM_TRY(scalar_impl<float>(s, f, s->W2, st, kChebScalar, true));
-    SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));
+    SGM_TRY(solve());
     return backward_impl<float>(s, s->W2, u, st, true);
   }
   SGM_TRY(scalar_impl<double>(s, f, s->W2, st, kChebScalar));
-  SGM_TRY(solve_impl<double>(s, basis, a, b, c, s->W2, s->W2, st));
+  SGM_TRY(solve());
   return backward_impl<double>(s, s->W2, u, st);
 }
 

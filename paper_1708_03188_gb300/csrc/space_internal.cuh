@@ -53,6 +53,8 @@ struct sgm_space {
   void* P1 = nullptr;
   void* P2 = nullptr;
   bool stream = false;
+  // sgm_space_solve_events: events recorded around the elimination of the physical-to-physical solves
+  cudaEvent_t ev_solve_begin = nullptr, ev_solve_end = nullptr;
   int hp = 0;
   long inner_p = 0;          // padded column count of the intermediates (M1 hp, or hp)
   CUtensorMap map_w1, map_w1s;
@@ -87,9 +89,9 @@ int build_project_table(sgm_space* s);
 // (a Dirichlet problem a lap(u) + b u = f is (0, a, b): its tables have S = 0), on spectral data
 // of type TS (float or double)
 int legendre_build(sgm_space* s, bool tc_images);
-// streaming Chebyshev passes (k_stream.cu): lengths with a kernel, the launch (mode kChebScalar:
-// map over the complex64 intermediate, FP64 spectral out; kChebBackward: map over the FP64
-// spectral intermediate, complex64 out) and the tensor-map encoder (tma.cuh)
+// streaming passes (k_stream.cu): lengths with a kernel, the launches (Chebyshev mode
+// kChebScalar: map over the complex64 intermediate, FP64 spectral out; kChebBackward: map over
+// the complex64 spectral solution, transformed in place) and the tensor-map encoder (tma.cuh)
 bool cheb_stream_length(int N);
 cudaError_t launch_cheb_stream(int mode, int N, const CUtensorMap& map, void* out, long inner, int basis,
                                const float2* twf, const float2* dctw, cudaStream_t s);

@@ -30,6 +30,7 @@ _SIGNATURES = {
     "sgm_space_destroy": (ctypes.c_int, [_VP]),
     "sgm_space_shape": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]),
     "sgm_space_cheb_method": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_int)]),
+    "sgm_space_solve_events": (ctypes.c_int, [_VP, _VP, _VP]),
     "sgm_tc_wait_timeouts": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
     "sgm_scalar_product": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "sgm_forward": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -146,6 +147,17 @@ class Space:
         out = (ctypes.c_int64 * len(self.kinds))()
         check(lib().sgm_space_shape(self._h, which, out))
         return tuple(int(v) for v in out)
+
+    def solve_events(self, begin=None, end=None):
+        """Record torch.cuda.Event `begin` / `end` around the elimination of every later
+        physical-to-physical solve of this space (None, None clears them)."""
+        def handle(ev):
+            if ev is None:
+                return None
+            if not ev.cuda_event:   # torch creates the CUDA event on its first record
+                ev.record()
+            return _VP(ev.cuda_event)
+        check(lib().sgm_space_solve_events(self._h, handle(begin), handle(end)))
 
     @property
     def cheb_method(self):

@@ -52,3 +52,32 @@ def test_stream_solve_against_oracle(kinds, sizes, coef):
     assert e < 2e-5
     assert tc_wait_timeouts() == 0
     sp.close()
+
+
+@pytest.mark.parametrize("kinds,sizes", [(["biharmonic", "c2c", "r2c"], [64, 64, 64]),
+                                         (["dirichlet", "c2c", "r2c"], [64, 32, 64])])
+def test_solve_events_bracket_the_elimination(kinds, sizes):
+    """sgm_space_solve_events: the events are recorded around the elimination of every solve
+    until cleared, the elimination takes a positive part of the solve, and the result is the
+    one without events."""
+    from paper_1708_03188_gb300.sgm import SgmError, Space
+    sp = Space(kinds, sizes, precision="f32")
+    g = inputs.rng("box3d", 880 + sizes[0])
+    f = torch.from_numpy(g.standard_normal(sizes)).float().cuda()
+    solve = (lambda: sp.biharmonic(1.0, 0.0, 0.0, f)) if kinds[0] == "biharmonic" else \
+        (lambda: sp.helmholtz(-1.0, 0.0, f))
+    plain = solve()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp.solve_events(a, b)
+    t0.record()
+    got = solve()
+    t1.record()
+    torch.cuda.synchronize()
+    inner, outer = a.elapsed_time(b), t0.elapsed_time(t1)
+    assert 0.0 < inner <= outer
+    assert torch.equal(got, plain)
+    sp.solve_events()
+    with pytest.raises(SgmError):
+        sp.solve_events(a, None)
+    sp.close()
