@@ -383,6 +383,24 @@ int sgm_adamw_step(float* w, void* w_bf16, const float* g, float* m, float* v, i
 int sgm_mse_grad(const float* out, const float* target, float* grad, float* loss, int64_t n, void* stream);
 /* Keep the wavenumbers of an Mc x Mc grid from B complex64 Mf x Mf spectral arrays (FFT order). */
 int sgm_spectral_truncate(const void* src, int Mf, void* dst, int Mc, int B, void* stream);
+/*
+ * Training batch of the learned closure (no counterpart in the paper: a data transform built
+ * from the symmetries of the Ginzburg-Landau equation, Sec. 6 - the equation is invariant under
+ * a global phase u -> exp(i theta) u, periodic translations, the transposition of the square
+ * grid and the reflections x -> -x, y -> -y).  For b < B, with k = idx[b], the complex64 fields
+ * u[k] and d[k] of the pools u, d ([n][M][M], device) are multiplied by phase[b] (B complex64
+ * values, device), rolled by (sx, sy) along axes (0, 1) (value at (i, j) moves to
+ * ((i + sx) mod M, (j + sy) mod M)), transposed when SGM_AUG_TRANSPOSE, then reflected along
+ * axis 0 (SGM_AUG_FLIP0: index i -> (M - i) mod M) and axis 1 (SGM_AUG_FLIP1), and written as
+ * FP32 channels xu[b][0] = su Re, xu[b][1] = su Im ([B][2][M][M], device), and xd from d with sd.
+ * idx: B int32 (device), each in [0, n); an entry outside writes zeros for that sample.
+ * sx, sy >= 0, flags a combination of SGM_AUG_* (SGM_ERR_ARG otherwise).
+ */
+#define SGM_AUG_TRANSPOSE 1
+#define SGM_AUG_FLIP0 2
+#define SGM_AUG_FLIP1 4
+int sgm_augment_pack(const void* u, const void* d, int n, int M, const int* idx, const void* phase, int B, int sx,
+                     int sy, int flags, float su, float sd, float* xu, float* xd, void* stream);
 /* x[b,0] = scale Re u[b], x[b,1] = scale Im u[b] (complex64 -> BF16 channels, B x H x W fields). */
 int sgm_pack_channels(const void* u, void* x, int B, int H, int W, float scale, void* stream);
 /* u[b] += scale (d[b,0] + i d[b,1]) (FP32 channels added to complex64 fields). */

@@ -179,19 +179,37 @@ def augment(u, d, gen):
 
 def train(net, x, target, iters=400, batch=16, lr=2e-3, seed=0, log=None, symmetries=True):
     """Minimise the MSE between net(x) and the scaled target with AdamW and a cosine learning-
-    rate decay, each minibatch transformed by a random symmetry of the equation (augment);
-    returns the loss history and the target scale (the network predicts target / scale)."""
+    rate decay, each minibatch transformed by a random symmetry of the equation (the transform of
+    augment, done on the device by sgm.augment_pack); returns the loss history and the target
+    scale (the network predicts target / scale).
+
+    Every minibatch's pool indices, phases, translation and reflections are drawn up front from
+    the host generator and uploaded once, so an iteration is device work only: one transform
+    launch, the network's kernels and the AdamW step."""
     scale_t = 1.0 / max(float(target.abs().pow(2).mean().sqrt()), 1e-30)
-    n = x.shape[0]
+    n, M = x.shape[0], x.shape[-1]
+    nb = min(batch, n)
     gen = torch.Generator(device="cpu").manual_seed(inputs.SEED_BASE + 4100 + seed)
+    idx_all = torch.randint(0, n, (iters, nb), generator=gen).to(torch.int32)
+    if symmetries:
+        theta = torch.rand(iters, nb, generator=gen, dtype=torch.float64) * (2 * math.pi)
+        shift = torch.randint(0, M, (iters, 2), generator=gen).tolist()
+        bits = torch.randint(0, 2, (iters, 3), generator=gen).tolist()
+        flags = [t * sgm.AUG_TRANSPOSE + f0 * sgm.AUG_FLIP0 + f1 * sgm.AUG_FLIP1 for t, f0, f1 in bits]
+    else:
+        theta = torch.zeros(iters, nb, dtype=torch.float64)
+        shift = [[0, 0]] * iters
+        flags = [0] * iters
+    idx_all = idx_all.cuda()
+    ph_all = torch.polar(torch.ones_like(theta), theta).to(torch.complex64).cuda()
+    xs, ts = x.contiguous(), target.contiguous()
+    xb = torch.empty((nb, 2, M, M), dtype=torch.float32, device="cuda")
+    tb = torch.empty_like(xb)
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     hist = []
     for it in range(iters):
-        idx = torch.randint(0, n, (min(batch, n),), generator=gen).cuda()
-        ub, db = x[idx], target[idx]
-        if symmetries:
-            ub, db = augment(ub, db, gen)
-        xb, tb = as_channels(ub, 1.0), as_fp32_channels(db, scale_t)
+        sgm.augment_pack(xs, ts, idx_all[it], ph_all[it], shift[it][0], shift[it][1], flags[it], 1.0, scale_t,
+                         xb, tb)
         out = net.forward(xb)
         gout = torch.empty_like(out)
         loss.zero_()

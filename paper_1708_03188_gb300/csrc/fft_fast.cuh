@@ -40,6 +40,10 @@ __host__ __device__ constexpr bool fast_length(int L) {
 }
 
 __host__ __device__ constexpr int pad_ld(int L) { return L + L / 16 + 1; }
+// Line stride for buffers whose lines are only read along the line (row tiles): congruent to 8
+// modulo 16 complex slots, so the two lines a half-warp touches in a pass of fewer than 16
+// butterflies per line (the first pass at L = 32, 64, 128) land on disjoint halves of the banks.
+__host__ __device__ constexpr int row_ld(int L) { return (L + L / 16 + 7) / 16 * 16 + 8; }
 __device__ __forceinline__ constexpr int padi(int e) { return e + (e >> 4); }
 
 // radix-16 butterfly as 4 x 4: inner DFT4 over n1 of x[s0 + 4 n1], twiddle W16^(s0 q),
@@ -86,12 +90,11 @@ template <int R, bool INV, typename C> __device__ __forceinline__ void butterfly
 
 // One pass over LINES lines held in `buf`; NTHREADS threads; TWO = offset of this pass's
 // twiddle table in `tw`.
-template <int L, int R, int NS, int TWO, int LINES, int NTHREADS, bool INV, typename C>
+template <int L, int R, int NS, int TWO, int LINES, int NTHREADS, bool INV, int LDP, typename C>
 __device__ __forceinline__ void fast_pass(C* buf, int nlines, const C* __restrict__ tw) {
   constexpr int LR = L / R;
   constexpr int TOTAL = LINES * LR;
   constexpr int M = (TOTAL + NTHREADS - 1) / NTHREADS;
-  constexpr int LDP = pad_ld(L);
   C v[M][R];
   const int active = nlines * LR;
 #pragma unroll
@@ -130,19 +133,20 @@ __device__ __forceinline__ void fast_pass(C* buf, int nlines, const C* __restric
   __syncthreads();
 }
 
-template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, typename C>
+template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, int LDP, typename C>
 __device__ __forceinline__ void fast_passes(C*, int, const C*, Radices<>) {}
 
-template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, typename C, int R, int... Rest>
+template <int L, int NS, int TWO, int LINES, int NTHREADS, bool INV, int LDP, typename C, int R, int... Rest>
 __device__ __forceinline__ void fast_passes(C* buf, int nlines, const C* tw, Radices<R, Rest...>) {
-  fast_pass<L, R, NS, TWO, LINES, NTHREADS, INV>(buf, nlines, tw);
-  fast_passes<L, NS * R, TWO + NS * R, LINES, NTHREADS, INV>(buf, nlines, tw, Radices<Rest...>{});
+  fast_pass<L, R, NS, TWO, LINES, NTHREADS, INV, LDP>(buf, nlines, tw);
+  fast_passes<L, NS * R, TWO + NS * R, LINES, NTHREADS, INV, LDP>(buf, nlines, tw, Radices<Rest...>{});
 }
 
-// In-place transform of `nlines` (<= LINES) padded lines; ends with __syncthreads().
-template <int L, int LINES, int NTHREADS, bool INV, typename C>
+// In-place transform of `nlines` (<= LINES) padded lines, LDP complex values apart (element e
+// at e + e/16 within its line); ends with __syncthreads().
+template <int L, int LINES, int NTHREADS, bool INV, int LDP = pad_ld(L), typename C>
 __device__ __forceinline__ void fft_fast(C* buf, int nlines, const C* __restrict__ tw) {
-  fast_passes<L, 1, 0, LINES, NTHREADS, INV>(buf, nlines, tw, typename FastRadices<L>::type{});
+  fast_passes<L, 1, 0, LINES, NTHREADS, INV, LDP>(buf, nlines, tw, typename FastRadices<L>::type{});
 }
 
 // ---- the same passes with other shared-memory layouts ------------------------------------------

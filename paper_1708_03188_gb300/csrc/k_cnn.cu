@@ -216,6 +216,43 @@ __global__ void k_pack(const float2* __restrict__ u, __nv_bfloat16* __restrict__
     x[(b * 2 + 1) * plane + p] = __float2bfloat16_rn(v.y * scale);
   }
 }
+// ---- training batch: pool gather + symmetry transform + (Re, Im) channels -------------------------
+// Output pixel (i, j) of sample b comes from the pool field idx[b] at the position the transform
+// sends there: undo the reflections (i -> (M - i) mod M on a reflected axis), then the
+// transposition, then the translation by (sx, sy); the value is multiplied by phase[b].
+__global__ void k_augment_pack(const float2* __restrict__ u, const float2* __restrict__ d, int n, int M,
+                               const int* __restrict__ idx, const float2* __restrict__ phase, int B, int sx, int sy,
+                               int flags, float su, float sd, float* __restrict__ xu, float* __restrict__ xd) {
+  const long plane = (long)M * M;
+  for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)B * plane; t += (long)gridDim.x * blockDim.x) {
+    const int b = (int)(t / plane);
+    const int p = (int)(t - (long)b * plane);
+    int i = p / M, j = p - (p / M) * M;
+    if (flags & SGM_AUG_FLIP0) i = (M - i) % M;
+    if (flags & SGM_AUG_FLIP1) j = (M - j) % M;
+    if (flags & SGM_AUG_TRANSPOSE) {
+      const int k = i;
+      i = j;
+      j = k;
+    }
+    i = (i - sx % M + M) % M;
+    j = (j - sy % M + M) % M;
+    const int k = idx[b];
+    float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    if (k >= 0 && k < n) {
+      const float2 w = phase[b];
+      const long src = (long)k * plane + (long)i * M + j;
+      const float2 uv = u[src], dv = d[src];
+      a = make_float2(uv.x * w.x - uv.y * w.y, uv.x * w.y + uv.y * w.x);
+      c = make_float2(dv.x * w.x - dv.y * w.y, dv.x * w.y + dv.y * w.x);
+    }
+    xu[((long)b * 2) * plane + p] = su * a.x;
+    xu[((long)b * 2 + 1) * plane + p] = su * a.y;
+    xd[((long)b * 2) * plane + p] = sd * c.x;
+    xd[((long)b * 2 + 1) * plane + p] = sd * c.y;
+  }
+}
+
 __global__ void k_unpack_add(const float* __restrict__ d, float2* __restrict__ u, long plane, int B, float scale) {
   for (long t = blockIdx.x * (long)blockDim.x + threadIdx.x; t < (long)B * plane; t += (long)gridDim.x * blockDim.x) {
     const long b = t / plane, p = t % plane;
@@ -386,6 +423,19 @@ int sgm_pack_channels(const void* u, void* x, int B, int H, int W, float scale, 
   const long plane = (long)H * W;
   k_pack<<<grid_for(B * plane), 256, 0, (cudaStream_t)stream>>>((const float2*)u, (__nv_bfloat16*)x, plane, B, scale);
   return launched("pack channels");
+}
+
+int sgm_augment_pack(const void* u, const void* d, int n, int M, const int* idx, const void* phase, int B, int sx,
+                     int sy, int flags, float su, float sd, float* xu, float* xd, void* stream) {
+  if (!u || !d || !idx || !phase || !xu || !xd) return set_error(SGM_ERR_NULL, "NULL pointer");
+  if (n < 1 || M < 1 || B < 1) return set_error(SGM_ERR_SIZE, "n, M and B must be positive");
+  if (sx < 0 || sy < 0 || (flags & ~(SGM_AUG_TRANSPOSE | SGM_AUG_FLIP0 | SGM_AUG_FLIP1)))
+    return set_error(SGM_ERR_ARG, "shifts must be >= 0 and flags a combination of SGM_AUG_*");
+  const long total = (long)B * M * M;
+  k_augment_pack<<<grid_for(total), 256, 0, (cudaStream_t)stream>>>((const float2*)u, (const float2*)d, n, M, idx,
+                                                                    (const float2*)phase, B, sx, sy, flags, su, sd,
+                                                                    xu, xd);
+  return launched("augment pack");
 }
 
 int sgm_unpack_add(const float* d, void* u, int B, int H, int W, float scale, void* stream) {

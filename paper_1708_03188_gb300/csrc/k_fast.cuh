@@ -229,54 +229,55 @@ __device__ __forceinline__ void cheb_forward_finish(cplx<T>* buf, int nt, long t
 template <typename T, int N, bool COLS = false>
 __device__ __forceinline__ void cheb_backward_prepare(cplx<T>* buf, int nt, int basis, const cplx<T>* __restrict__ dctw) {
   using C = cplx<T>;
-  using I = TileIdx<COLS, N, fast_tw_cols<T>()>;
-  constexpr int PER = (N * fast_tw_cols<T>() + kFastThreads - 1) / kFastThreads;
-  C a[PER];
+  constexpr int TW = fast_tw_cols<T>();
+  using I = TileIdx<COLS, N, TW>;
+  constexpr int HALF = N / 2;
+  constexpr int PH = (HALF * TW + kFastThreads - 1) / kFastThreads;
+  // Shen stencil in place, in two halves of the rows: the upper half (k >= N/2) first, whose reads
+  // (rows k, k - 2, k - 4) all still hold coefficients, then the lower half, which reads only rows
+  // below N/2, untouched by the first half's writes.  Half the rows per round halves the values a
+  // thread holds across the synchronisation.
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * kFastThreads;
-    const int t = I::line(idx), k = I::pos(idx);
-    if (t < nt) {
-      C v = buf[I::at(t, k)];
-      if (basis == kDirichlet) {
-        if (k >= 2) v = csub(v, buf[I::at(t, k - 2)]);
-      } else if (basis == kNeumann) {
-        if (k >= 2) { const T q = neumann_q<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x -= q * u.x; v.y -= q * u.y; }
-      } else if (basis == kBiharmonic) {
-        if (k >= 2) { const T be = fbeta<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x += be * u.x; v.y += be * u.y; }
-        if (k >= 4) { const T ga = fgamma<T>(k - 4); const C u = buf[I::at(t, k - 4)]; v.x += ga * u.x; v.y += ga * u.y; }
-      }
-      a[q] = v;
-    }
-  }
-  __syncthreads();
+  for (int h = 1; h >= 0; --h) {
+    C a[PH];
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * kFastThreads;
-    const int t = I::line(idx), k = I::pos(idx);
-    if (t < nt) buf[I::at(t, k)] = a[q];
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * kFastThreads;
-    const int t = I::line(idx), k = I::pos(idx);
-    if (t < nt) {
-      if (k == 0) {
-        a[q] = buf[I::at(t, 0)];
-      } else {
-        const C x = buf[I::at(t, k)], y = buf[I::at(t, N - k)];
-        const C d = mk<C>(x.x + y.y, x.y - y.x);
-        a[q] = cscale(cmulc(d, __ldg(&dctw[k])), (T)0.5);
+    for (int q = 0; q < PH; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = COLS ? idx % TW : idx / HALF, k = h * HALF + (COLS ? idx / TW : idx % HALF);
+      if (idx < HALF * TW && t < nt) {
+        C v = buf[I::at(t, k)];
+        if (basis == kDirichlet) {
+          if (k >= 2) v = csub(v, buf[I::at(t, k - 2)]);
+        } else if (basis == kNeumann) {
+          if (k >= 2) { const T q2 = neumann_q<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x -= q2 * u.x; v.y -= q2 * u.y; }
+        } else if (basis == kBiharmonic) {
+          if (k >= 2) { const T be = fbeta<T>(k - 2); const C u = buf[I::at(t, k - 2)]; v.x += be * u.x; v.y += be * u.y; }
+          if (k >= 4) { const T ga = fgamma<T>(k - 4); const C u = buf[I::at(t, k - 4)]; v.x += ga * u.x; v.y += ga * u.y; }
+        }
+        a[q] = v;
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int q = 0; q < PER; ++q) {
-    const int idx = threadIdx.x + q * kFastThreads;
-    const int t = I::line(idx), k = I::pos(idx);
-    if (t < nt) buf[I::at(t, k)] = a[q];
+    for (int q = 0; q < PH; ++q) {
+      const int idx = threadIdx.x + q * kFastThreads;
+      const int t = COLS ? idx % TW : idx / HALF, k = h * HALF + (COLS ? idx / TW : idx % HALF);
+      if (idx < HALF * TW && t < nt) buf[I::at(t, k)] = a[q];
+    }
+    __syncthreads();
+  }
+  // DCT-III pre-twiddle: rows k and N - k of a line are formed from the same two values, so one
+  // thread reads both and writes both (row 0 is unchanged; row N/2 pairs with itself).
+  for (int idx = threadIdx.x; idx < HALF * TW; idx += kFastThreads) {
+    const int t = COLS ? idx % TW : idx / HALF, k = 1 + (COLS ? idx / TW : idx % HALF);
+    if (t >= nt) continue;
+    const C x = buf[I::at(t, k)], y = buf[I::at(t, N - k)];
+    const C d = mk<C>(x.x + y.y, x.y - y.x);
+    buf[I::at(t, k)] = cscale(cmulc(d, __ldg(&dctw[k])), (T)0.5);
+    if (k < HALF) {
+      const C e = mk<C>(y.x + x.y, y.y - x.x);
+      buf[I::at(t, N - k)] = cscale(cmulc(e, __ldg(&dctw[N - k])), (T)0.5);
+    }
   }
   __syncthreads();
 }

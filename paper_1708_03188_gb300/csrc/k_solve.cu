@@ -768,6 +768,21 @@ int solve_scratch_values(int basis, int nc) {
   return basis == kDirichlet ? 2 + 2 * nc : basis == kNeumann ? 3 + 2 * nc : 5 + 2 * nc;
 }
 
+// Dynamic shared memory that lets at most max_per_sm CTAs of a kernel share an SM.  The 3-D
+// biharmonic elimination runs one warp per SM sub-partition on 132 SMs, each warp's chain keeping
+// its sub-partition's FP64 pipe busy.  A launch that meets SMs partly filled by other kernels (the
+// elimination or transforms of a concurrent solve on another stream) would otherwise put two of
+// its CTAs on some SMs, whose sub-partitions would then serve two chains each and finish last.
+static size_t spread_smem(size_t need, int max_per_sm) {
+  int dev = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess || per_sm <= 0)
+    return need;
+  // every CTA also holds 1 KB of shared memory reserved by the system
+  const size_t cap = (size_t)per_sm / (size_t)(max_per_sm + 1) + 1;
+  return std::max(need, cap);
+}
+
 template <typename T, int NC, typename TO>
 static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
                             long ncols, const Wavenumbers& wn, const ColumnMap& cm, const double* tab, double* scratch,
@@ -813,7 +828,7 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
     if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     k_solve_dirichlet<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
   } else {
-    const size_t smem = sizeof(double) * 13 * ts;
+    const size_t smem = NC == 4 ? spread_smem(sizeof(double) * 13 * ts, 1) : sizeof(double) * 13 * ts;
     if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_biharmonic<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     k_solve_biharmonic<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, c, wn, cm, tab, ts, scratch);
   }

@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_rows_stream(const void* __r
                                                                  const float2* __restrict__ tw_L) {
   using C = float2;
   constexpr int LINES = 4096 / LF;
-  constexpr int LDP = pad_ld(LF);
+  constexpr int LDP = row_ld(LF);
   constexpr int H = LF;
   constexpr int L = 2 * LF;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -248,21 +248,34 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_rows_stream(const void* __r
         issue(nx, q);
       }
     }
-    fft_fast<LF, LINES, kFastThreads, MODE == kRowC2R>(buf, nl, twf);
+    fft_fast<LF, LINES, kFastThreads, MODE == kRowC2R, LDP>(buf, nl, twf);
     if (MODE == kRowR2C) {
+      // X_k from Z_k and Z_{H-k} (indices mod H): one thread forms the pair k, H - k from the same
+      // two values, k < H/2 running over aligned blocks of 16 (conflict-free loads of Z_k)
       C* dst = reinterpret_cast<C*>(out) + row0 * hp;
       const float sc = 0.5f / (float)L;
-      for (int idx = threadIdx.x; idx < nl * hp; idx += kFastThreads) {
-        const int line = idx / hp, k = idx - line * hp;
-        C r = mk<C>(0.f, 0.f);
-        if (k <= H) {
-          const C z = buf[line * LDP + padi(k == H ? 0 : k)];
-          const C zc = cconj(buf[line * LDP + padi(k == 0 ? 0 : H - k)]);
-          const C e = cadd(z, zc);
-          const C o = rot90<false>(cmul(__ldg(&tw_L[k]), csub(z, zc)));
-          r = cscale(cadd(e, o), sc);
+      auto coef = [&](const C z, const C zp, int k) {
+        const C zc = cconj(zp);
+        const C e = cadd(z, zc);
+        const C o = rot90<false>(cmul(__ldg(&tw_L[k]), csub(z, zc)));
+        return cscale(cadd(e, o), sc);
+      };
+      constexpr int HH = H / 2;
+      for (int idx = threadIdx.x; idx < nl * HH; idx += kFastThreads) {
+        const int line = idx / HH, k = idx - line * HH;
+        const C z = buf[line * LDP + padi(k)], zp = buf[line * LDP + padi(k == 0 ? 0 : H - k)];
+        dst[(long)line * hp + k] = coef(z, zp, k);
+        dst[(long)line * hp + H - k] = coef(zp, z, H - k);
+      }
+      // k = H/2, its own partner, and the padding columns H + 1 .. hp - 1
+      for (int idx = threadIdx.x; idx < nl * (hp - H); idx += kFastThreads) {
+        const int line = idx / (hp - H), c = idx - line * (hp - H);
+        if (c == 0) {
+          const C z = buf[line * LDP + padi(HH)];
+          dst[(long)line * hp + HH] = coef(z, z, HH);
+        } else {
+          dst[(long)line * hp + H + c] = mk<C>(0.f, 0.f);
         }
-        dst[idx] = r;
       }
     } else {
       C* dst = reinterpret_cast<C*>(out) + row0 * LF;
@@ -312,7 +325,7 @@ cudaError_t launch_rows_lf(const void* in, void* out, long nrows, int hp, const 
                            cudaStream_t s) {
   constexpr int LINES = 4096 / LF;
   const size_t stage = (size_t)LINES * (MODE == kRowR2C ? LF : hp) * sizeof(float2);
-  const size_t smem = kStages * stage + (size_t)LINES * pad_ld(LF) * sizeof(float2) + kStages * sizeof(uint64_t);
+  const size_t smem = kStages * stage + (size_t)LINES * row_ld(LF) * sizeof(float2) + kStages * sizeof(uint64_t);
   unsigned grid = 1;
   cudaError_t e = persistent_launch_params(k_rows_stream<MODE, LF>, smem, (nrows + LINES - 1) / LINES, &grid);
   if (e != cudaSuccess) return e;

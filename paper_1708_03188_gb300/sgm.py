@@ -63,6 +63,8 @@ _SIGNATURES = {
     "sgm_spectral_truncate": (ctypes.c_int, [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int, _VP]),
     "sgm_pack_channels": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
     "sgm_unpack_add": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_float, _VP]),
+    "sgm_augment_pack": (ctypes.c_int, [_VP, _VP, ctypes.c_int, ctypes.c_int, _VP, _VP, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float, _VP, _VP, _VP]),
     "sgm_alu_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _VP,
                                      ctypes.POINTER(_D), _VP]),
     "sgm_helmholtz_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -445,6 +447,25 @@ def pack_channels(u, x, scale, stream=None):
     B, H, W = u.shape
     check(lib().sgm_pack_channels(_ptr(u), _ptr(x), B, H, W, float(scale), _stream(stream)))
     return x
+
+
+AUG_TRANSPOSE, AUG_FLIP0, AUG_FLIP1 = 1, 2, 4
+
+
+def augment_pack(u, d, idx, phase, sx, sy, flags, su, sd, xu, xd, stream=None):
+    """Training batch of the closure: pool fields u[idx[b]], d[idx[b]] (complex64 [n, M, M]) times
+    phase[b] (complex64 [B]), rolled by (sx, sy), transposed / reflected per flags (AUG_*), as FP32
+    channels xu = su (Re, Im), xd = sd (Re, Im) ([B, 2, M, M]).  idx: int32 [B] on the device."""
+    n, M = u.shape[0], u.shape[-1]
+    B = idx.numel()
+    for t, dt in ((u, torch.complex64), (d, torch.complex64), (idx, torch.int32), (phase, torch.complex64),
+                  (xu, torch.float32), (xd, torch.float32)):
+        if t.dtype != dt or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"expected contiguous CUDA {dt}, got {t.dtype} (contiguous={t.is_contiguous()})")
+    if d.shape != u.shape or phase.numel() != B or xu.shape != (B, 2, M, M) or xd.shape != (B, 2, M, M):
+        raise ValueError("shapes: u, d [n, M, M]; idx, phase [B]; xu, xd [B, 2, M, M]")
+    check(lib().sgm_augment_pack(_ptr(u), _ptr(d), n, M, _ptr(idx), _ptr(phase), B, int(sx), int(sy), int(flags),
+                                 float(su), float(sd), _ptr(xu), _ptr(xd), _stream(stream)))
 
 
 def unpack_add(d, u, scale, stream=None):

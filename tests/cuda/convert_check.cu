@@ -1,6 +1,7 @@
 // Checks the integer-pipe conversions of csrc/convert.cuh bitwise against the hardware
 // conversions: widen_f32 on all 2^32 FP32 bit patterns, narrow_f64 on random doubles and on
-// constructed ties, near-ties, carries and range edges.  Prints "mismatches <n>"; exit 0.
+// constructed ties, near-ties, carries and range edges, including ties of results in the FP32
+// subnormal range.  Prints "mismatches <n>"; exit 0.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_1708_03188_gb300/csrc/convert.cuh"
@@ -37,6 +38,14 @@ __global__ void narrow_many(unsigned long long* bad, unsigned long long n) {
     if (kind == 4) mant = 0xfffffffffffffull;                        // carry into the exponent
     bits = sign | (ex << 52) | mant;
     if (kind == 5) bits = mix(r + 7);                                // any pattern
+    if (kind == 6 || kind == 7) {   // FP32-subnormal results: an exact tie (6), one unit above it (7)
+      const unsigned long long es = 873 + (mix(r + 3) % 24);      // 873..896
+      const unsigned sh = (unsigned)(926 - es);
+      unsigned long long M = (1ull << 52) | mant;
+      M = ((M >> sh) << sh) | (1ull << (sh - 1));
+      if (kind == 7) M += 1;
+      bits = sign | (es << 52) | (M & 0xfffffffffffffull);
+    }
     const double d = __longlong_as_double((long long)bits);
     const float a = sgm::narrow_f64(d), b = __double2float_rn(d);
     if (__float_as_uint(a) != __float_as_uint(b) && !(a != a && b != b)) atomicAdd(bad, 1ull);

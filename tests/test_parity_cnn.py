@@ -172,3 +172,48 @@ def test_fp32_input_layer():
     sgm.conv3x3_backward_weights(gy, x, gw, gb)
     gref = sum(ocnn.conv_backward(xo[i], wo, host(gy)[i])[1] for i in range(B))
     assert rel(host(gw), gref) < 2e-5
+
+
+@pytest.mark.parametrize("flags", [0, 1, 2, 4, 7, 6])
+def test_augment_pack_matches_the_symmetry_transform(flags):
+    """sgm_augment_pack against the same transform in plain torch ops on the gathered pool
+    fields: phase, roll by (sx, sy), transposition, reflections (i -> (M - i) mod M), channels."""
+    from paper_1708_03188_gb300 import sgm
+    g = torch.Generator().manual_seed(7000 + flags)
+    n, M, B = 9, 32, 5
+    u = torch.complex(torch.randn(n, M, M, generator=g), torch.randn(n, M, M, generator=g)).to(torch.complex64)
+    d = torch.complex(torch.randn(n, M, M, generator=g), torch.randn(n, M, M, generator=g)).to(torch.complex64)
+    idx = torch.tensor([3, 0, 8, 3, 5], dtype=torch.int32)
+    phase = torch.polar(torch.ones(B), torch.rand(B, generator=g) * 6.283185307179586).to(torch.complex64)
+    sx, sy, su, sd = 5, 30, 1.0, 2.5
+    xu = torch.empty(B, 2, M, M, device="cuda")
+    xd = torch.empty_like(xu)
+    sgm.augment_pack(u.cuda(), d.cuda(), idx.cuda(), phase.cuda(), sx, sy, flags, su, sd, xu, xd)
+
+    def ref(f, scale):
+        v = f[idx.long()].to(torch.complex128) * phase.to(torch.complex128).view(B, 1, 1)
+        v = torch.roll(v, (sx, sy), (1, 2))
+        if flags & sgm.AUG_TRANSPOSE:
+            v = v.transpose(1, 2)
+        rev = (-torch.arange(M)) % M
+        if flags & sgm.AUG_FLIP0:
+            v = v.index_select(1, rev)
+        if flags & sgm.AUG_FLIP1:
+            v = v.index_select(2, rev)
+        return torch.stack([v.real, v.imag], dim=1) * scale
+
+    for got, want in ((xu, ref(u, su)), (xd, ref(d, sd))):
+        err = (got.double().cpu() - want).abs().max().item()
+        assert err <= 2e-6 * want.abs().max().item()
+
+
+def test_augment_pack_rejects_bad_arguments():
+    from paper_1708_03188_gb300 import sgm
+    u = torch.zeros(2, 16, 16, dtype=torch.complex64, device="cuda")
+    idx = torch.zeros(3, dtype=torch.int32, device="cuda")
+    ph = torch.ones(3, dtype=torch.complex64, device="cuda")
+    x = torch.empty(3, 2, 16, 16, device="cuda")
+    with pytest.raises(sgm.SgmError):
+        sgm.augment_pack(u, u, idx, ph, -1, 0, 0, 1.0, 1.0, x, x.clone())
+    with pytest.raises(sgm.SgmError):
+        sgm.augment_pack(u, u, idx, ph, 0, 0, 8, 1.0, 1.0, x, x.clone())
