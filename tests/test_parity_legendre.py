@@ -141,8 +141,12 @@ def test_legendre_errors():
         Space(["legendre_dirichlet", "r2c"], [129, 8], precision="f32", cheb="tc")   # N <= 128 on the tensor cores
     with pytest.raises(SgmError):
         Space(["legendre_dirichlet", "r2c"], [32, 8], precision="f64", cheb="tc")
-    with pytest.raises(SgmError):
-        Space(["c2c", "legendre"], [8, 8], precision="f64")
+    with pytest.raises(SgmError):   # at most one polynomial axis
+        Space(["legendre", "legendre_dirichlet"], [8, 8], precision="f64")
+    # a Legendre axis after a Fourier axis is the axes option of Sec. 4: a permuted view
+    ps = Space(["c2c", "legendre"], [8, 6], precision="f64")
+    assert ps.spectral_shape == (8, 6)
+    ps.close()
     gs = gspace(["legendre_biharmonic", "c2c"], [16, 8], "f64")
     x = torch.zeros(gs.spectral_shape, dtype=gs.spectral_dtype, device="cuda")
     with pytest.raises(SgmError):
