@@ -139,5 +139,20 @@ cudaError_t launch_solve(int basis, bool real, double a, double b, double c, con
 cudaError_t launch_solve_f64_to_f32(int basis, double a, double b, double c, const void* in, void* out, int N, long ncols,
                                     const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
                                     const int2* groups, long ngroups, cudaStream_t s);
+// Factored eliminations of 3-D spaces (k_solve.cu): FP64 values per row and work thread of a
+// factorisation table (0: the basis has none), work threads of the table for a call's column
+// layout (0: a 1-D or 2-D space, no factored form), the factorisation of the operator (a, b, c)
+// into a table of rows x values x threads doubles, and the solve replaying a table (TI, TO:
+// spectral input and output types; the table must come from launch_factor with the same
+// basis, N, columns and wavenumbers).  The factored forms take one thread per pair of columns of a
+// 3-D space: groups must be null.
+int solve_factor_values(int basis);
+long solve_factor_threads(long ncols, const Wavenumbers& wn, const int2* groups, long ngroups);
+cudaError_t launch_factor(int basis, double a, double b, double c, int N, long ncols, const Wavenumbers& wn,
+                          const double* tab, const int2* groups, long ngroups, double* fact, cudaStream_t s);
+template <typename TI, typename TO>
+cudaError_t launch_solve_factored_to(int basis, bool real, const void* in, void* out, int N, long ncols,
+                                     const Wavenumbers& wn, const double* tab, const double* fact, double* scratch,
+                                     long scratch_threads, const int2* groups, long ngroups, cudaStream_t s);
 
 }  // namespace sgm

@@ -763,6 +763,419 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
   }
 }
 
+// ---- factored eliminations (3-D spaces, NC = 2 or 4) -------------------------------------
+// The factorisation of one (column group, parity) system - reciprocal pivots, multipliers, the
+// reduced super-diagonals and tail coefficients - depends only on the operator (a, b, c) and on
+// kappa2, not on the right-hand side, just as the paper's Helmholtz and Biharmonic solver objects
+// are built once from their matrices and then applied to many right-hand sides (Sec. 4).
+// k_factor_* runs the top-down factorisation of the kernels above and stores it per work item in
+// a table laid out [row][value][work thread] (work thread = 32 * warp + lane of the work
+// decomposition above, so a warp reads 256 contiguous bytes per value); k_solve_*_f replays only
+// the right-hand-side recurrences from the table.  Both use one thread per pair of columns +-l1
+// (NC = 2): without the factorisation to share, four columns per thread would only halve the warps
+// that hide the FP64 latency.  FP64 operations per row and complex column: Dirichlet 10 (against 16
+// with the factorisation shared by a pair), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal pivots are the same FP64
+// values the kernels above compute; the back substitution adds the term of the unknown just
+// solved last, so that its dependent chain is one FMA and one multiply per row.
+enum { FD_MU = 0, FD_R, FD_G, FD_GE, FD_COUNT };                        // Dirichlet table values
+enum { FB_MU = 0, FB_MU1, FB_R, FB_U1, FB_U2, FB_H0, FB_H1, FB_COUNT };  // biharmonic table values
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_factor_dirichlet(int N, double a, double b,
+                                                          const __grid_constant__ Wavenumbers wn,
+                                                          const __grid_constant__ ColumnMap cm,
+                                                          const double* __restrict__ tab, int ts,
+                                                          double* __restrict__ fact) {
+  extern __shared__ double sh[];
+  double* aA0 = sh;
+  double* aG = sh + ts;
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    aA0[k] = a * tab[TD_A0 * ts + k];
+    aG[k] = a * tab[TD_G * ts + k];
+  }
+  __syncthreads();
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long nwb = (cm.nitems + 31) / 32;
+  const long TT = 2 * nwb * 32;
+  const int nb = N - 2;
+  const double half_pi = 1.5707963267948966;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
+    const int p = (int)(w & 1);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
+    const double k2 = kappa2_of(wn, cc[0]);
+    const double aB = b - a * k2;
+    const double ell = -aB * half_pi;
+    const double aBpi = aB * 3.141592653589793;
+    const int n = (nb - p + 1) / 2;
+    double* fr = fact + w * 32 + lane;
+    double pr = 0.0, pge = 0.0, pg = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int k = p + 2 * i;
+      double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
+      double g = aG[k];
+      double mu = 0.0;
+      if (i > 0) {
+        mu = ell * pr;
+        d = fma(-mu, pge, d);
+        g = fma(-mu, pg, g);
+      }
+      const double r = rcp64(d);
+      fr[FD_MU * TT] = mu;
+      fr[FD_R * TT] = r;
+      fr[FD_G * TT] = g;
+      fr[FD_GE * TT] = g + ell;
+      fr += FD_COUNT * TT;
+      pr = r; pg = g; pge = g + ell;
+    }
+  }
+}
+
+// The factored sweeps do little FP64 work per row (the Dirichlet forward sweep 2 FMAs per
+// column), so every value is stored one row after it is computed: in-order issue would otherwise
+// hold the store, and the warp behind it, until the FMA that produced the value completes.
+template <typename T, int NC, typename TO = T>
+__global__ void __launch_bounds__(128) k_solve_dirichlet_f(const void* __restrict__ in, void* __restrict__ out, int N,
+                                                           long ncols, const __grid_constant__ ColumnMap cm,
+                                                           const double* __restrict__ fact,
+                                                           double* __restrict__ scratch) {
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long nwb = (cm.nitems + 31) / 32;
+  const long TT = 2 * nwb * 32;
+  const long fs = FD_COUNT * TT;   // table stride of one row
+  const int nb = N - 2;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
+    const int p = (int)(w & 1);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
+    const int n = (nb - p + 1) / 2;
+    const double* fr = fact + w * 32 + lane;
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    const long rstep = 2 * ncols;
+    // forward: f'_i = f_i - mu_i f'_{i-1} into the scratch; operands loaded one row ahead
+    double2 fn[NC], pf[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      fn[q] = n > 0 ? ld2<T>(in, off[q], false) : make_double2(0.0, 0.0);
+      pf[q] = make_double2(0.0, 0.0);
+    }
+    double mun = n > 0 ? fr[FD_MU * TT] : 0.0;
+    double* s = scratch + gt;
+    const long sstep = (long)(2 * NC) * nth;
+    for (int i = 0; i < n; ++i) {
+      const double mu = mun;
+      double2 f[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q] = fn[q];
+        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, false);
+      }
+      if (i + 1 < n) mun = fr[(long)(i + 1) * fs + FD_MU * TT];
+      if (i > 0) {   // row i - 1
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          s[(2 * q) * nth] = pf[q].x;
+          s[(2 * q + 1) * nth] = pf[q].y;
+        }
+        s += sstep;
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q].x = fma(-mu, pf[q].x, f[q].x);
+        f[q].y = fma(-mu, pf[q].y, f[q].y);
+        pf[q] = f[q];
+      }
+    }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        s[(2 * q) * nth] = pf[q].x;
+        s[(2 * q + 1) * nth] = pf[q].y;
+      }
+    }
+    // backward: u_i = (f'_i - g_i sum_{j>=i+2} u_j - (g_i + ell) u_{i+1}) r_i; s points at row n-1
+    double2 un[NC], Tp[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) { un[q] = make_double2(0.0, 0.0); Tp[q] = make_double2(0.0, 0.0); }
+    double vn[2 * NC], rn = 0.0, gn = 0.0, gen = 0.0;
+    if (n > 0) {
+#pragma unroll
+      for (int v = 0; v < 2 * NC; ++v) vn[v] = s[v * nth];
+      const double* fl = fr + (long)(n - 1) * fs;
+      rn = fl[FD_R * TT]; gn = fl[FD_G * TT]; gen = fl[FD_GE * TT];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      double v[2 * NC];
+#pragma unroll
+      for (int j = 0; j < 2 * NC; ++j) v[j] = vn[j];
+      const double r = rn, g = gn, ge = gen;
+      if (i > 0) {
+        s -= sstep;
+#pragma unroll
+        for (int j = 0; j < 2 * NC; ++j) vn[j] = s[j * nth];
+        const double* fl = fr + (long)(i - 1) * fs;
+        rn = fl[FD_R * TT]; gn = fl[FD_G * TT]; gen = fl[FD_GE * TT];
+      }
+      // row i + 1 is stored one iteration late
+      if (i + 1 < n) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) st2<TO>(out, off[q] + (long)(i + 1) * rstep, false, un[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        double2 u;
+        u.x = fma(-ge, un[q].x, fma(-g, Tp[q].x, v[2 * q])) * r;
+        u.y = fma(-ge, un[q].y, fma(-g, Tp[q].y, v[2 * q + 1])) * r;
+        Tp[q].x += un[q].x;
+        Tp[q].y += un[q].y;
+        un[q] = u;
+      }
+    }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, off[q], false, un[q]);
+    }
+    for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], false, make_double2(0.0, 0.0));
+    }
+  }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(128) k_factor_biharmonic(int N, double a, double b, double cc0,
+                                                           const __grid_constant__ Wavenumbers wn,
+                                                           const __grid_constant__ ColumnMap cm,
+                                                           const double* __restrict__ tab, int ts,
+                                                           double* __restrict__ fact) {
+  extern __shared__ double sh[];
+  enum { SS0 = 0, SS1, SS2, SG0, SG1, SB0, SB2, SB4, SALO, SA0, SAUP, SF0, SF1, SCOUNT };
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    sh[SS0 * ts + k] = a * tab[TB_S0 * ts + k];
+    sh[SS1 * ts + k] = a * tab[TB_S1 * ts + k];
+    sh[SS2 * ts + k] = a * tab[TB_S2 * ts + k];
+    sh[SG0 * ts + k] = a * tab[TB_G0 * ts + k];
+    sh[SG1 * ts + k] = a * tab[TB_G1 * ts + k];
+    sh[SB0 * ts + k] = tab[TB_B0 * ts + k];
+    sh[SB2 * ts + k] = tab[TB_B2 * ts + k];
+    sh[SB4 * ts + k] = tab[TB_B4 * ts + k];
+    sh[SALO * ts + k] = tab[TB_ALO * ts + k];
+    sh[SA0 * ts + k] = tab[TB_A0 * ts + k];
+    sh[SAUP * ts + k] = tab[TB_AUP * ts + k];
+    sh[SF0 * ts + k] = tab[TB_F0 * ts + k];
+    sh[SF1 * ts + k] = tab[TB_F1 * ts + k];
+  }
+  __syncthreads();
+  auto tb = [&](int t, int k) -> double { return sh[t * ts + k]; };
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long nwb = (cm.nitems + 31) / 32;
+  const long TT = 2 * nwb * 32;
+  const int nb = N - 4;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
+    const int p = (int)(w & 1);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
+    const double k2 = kappa2_of(wn, cc[0]);
+    const double aA = b - 2.0 * a * k2;
+    const double aB = fma(a * k2, k2, fma(-b, k2, cc0));
+    const int n = (nb - p + 1) / 2;
+    double r1 = 0, U11 = 0, U21 = 0, g01 = 0, g11 = 0, q41 = 0;
+    double r2 = 0, U12 = 0, U22 = 0, g02 = 0, g12 = 0, q42 = 0;
+    double* fr = fact + w * 32 + lane;
+    for (int i = 0; i < n; ++i) {
+      const int k = p + 2 * i;
+      const double q4 = aB * tb(SB4, k);
+      double D = fma(aA, tb(SA0, k), fma(aB, tb(SB0, k), tb(SS0, k)));
+      double u1 = fma(aA, tb(SAUP, k), fma(aB, tb(SB2, k), tb(SS1, k)));
+      double u2 = tb(SS2, k) + q4;
+      double h0 = tb(SG0, k), h1 = tb(SG1, k);
+      const double F0a = tb(SF0, k + 2), F1a = tb(SF1, k + 2);
+      const double F0b = tb(SF0, k + 4), F1b = tb(SF1, k + 4);
+      double mu = 0.0, mu1 = 0.0;
+      if (i >= 1) {
+        double L1 = fma(aA, tb(SALO, k), aB * tb(SB2, k - 2));
+        if (i >= 2) {
+          mu = q42 * r2;
+          L1 = fma(-mu, U12, L1);
+          D = fma(-mu, U22, D);
+          u1 = fma(-mu, fma(g02, F0a, g12 * F1a), u1);
+          u2 = fma(-mu, fma(g02, F0b, g12 * F1b), u2);
+          h0 = fma(-mu, g02, h0);
+          h1 = fma(-mu, g12, h1);
+        }
+        mu1 = L1 * r1;
+        D = fma(-mu1, U11, D);
+        u1 = fma(-mu1, U21, u1);
+        u2 = fma(-mu1, fma(g01, F0b, g11 * F1b), u2);
+        h0 = fma(-mu1, g01, h0);
+        h1 = fma(-mu1, g11, h1);
+      }
+      const double r = rcp64(D);
+      fr[FB_MU * TT] = mu;
+      fr[FB_MU1 * TT] = mu1;
+      fr[FB_R * TT] = r;
+      fr[FB_U1 * TT] = u1;
+      fr[FB_U2 * TT] = u2;
+      fr[FB_H0 * TT] = h0;
+      fr[FB_H1 * TT] = h1;
+      fr += FB_COUNT * TT;
+      r2 = r1; U12 = U11; U22 = U21; g02 = g01; g12 = g11; q42 = q41;
+      r1 = r; U11 = u1; U21 = u2; g01 = h0; g11 = h1; q41 = q4;
+    }
+  }
+}
+
+template <typename T, int NC, typename TO = T>
+__global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restrict__ in, void* __restrict__ out,
+                                                            int N, long ncols, const __grid_constant__ ColumnMap cm,
+                                                            const double* __restrict__ tab, int ts,
+                                                            const double* __restrict__ fact,
+                                                            double* __restrict__ scratch) {
+  // shared: the rank-2 tail weights F0, F1 (zero past the basis)
+  extern __shared__ double sh[];
+  double* sF0 = sh;
+  double* sF1 = sh + ts;
+  for (int k = threadIdx.x; k < ts; k += blockDim.x) {
+    sF0[k] = tab[TB_F0 * ts + k];
+    sF1[k] = tab[TB_F1 * ts + k];
+  }
+  __syncthreads();
+  const long nth = (long)gridDim.x * blockDim.x;
+  const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const long nwb = (cm.nitems + 31) / 32;
+  const long TT = 2 * nwb * 32;
+  const long fs = FB_COUNT * TT;
+  const int nb = N - 4;
+  for (long w = gt / 32; w < 2 * nwb; w += nth / 32) {
+    const int p = (int)(w & 1);
+    const long item = (w >> 1) * 32 + lane;
+    if (item >= cm.nitems) continue;
+    long cc[NC];
+    map_columns<NC>(cm, item, cc);
+    const int n = (nb - p + 1) / 2;
+    const double* fr = fact + w * 32 + lane;
+    long off[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
+    const long rstep = 2 * ncols;
+    // forward: f'_i = f_i - mu_i f'_{i-2} - mu1_i f'_{i-1} (the multipliers are zero where the
+    // rows above do not exist); operands loaded one row ahead, each row stored one row late
+    double2 fn[NC], f1[NC], f2[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      fn[q] = n > 0 ? ld2<T>(in, off[q], false) : make_double2(0.0, 0.0);
+      f1[q] = f2[q] = make_double2(0.0, 0.0);
+    }
+    double mun = 0.0, mu1n = 0.0;
+    if (n > 0) { mun = fr[FB_MU * TT]; mu1n = fr[FB_MU1 * TT]; }
+    double* s = scratch + gt;
+    const long sstep = (long)(2 * NC) * nth;
+    for (int i = 0; i < n; ++i) {
+      const double mu = mun, mu1 = mu1n;
+      double2 f[NC];
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q] = fn[q];
+        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, false);
+      }
+      if (i + 1 < n) {
+        const double* fl = fr + (long)(i + 1) * fs;
+        mun = fl[FB_MU * TT];
+        mu1n = fl[FB_MU1 * TT];
+      }
+      if (i > 0) {   // row i - 1
+#pragma unroll
+        for (int q = 0; q < NC; ++q) {
+          s[(2 * q) * nth] = f1[q].x;
+          s[(2 * q + 1) * nth] = f1[q].y;
+        }
+        s += sstep;
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        f[q].x = fma(-mu1, f1[q].x, fma(-mu, f2[q].x, f[q].x));
+        f[q].y = fma(-mu1, f1[q].y, fma(-mu, f2[q].y, f[q].y));
+        f2[q] = f1[q];
+        f1[q] = f[q];
+      }
+    }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        s[(2 * q) * nth] = f1[q].x;
+        s[(2 * q + 1) * nth] = f1[q].y;
+      }
+    }
+    // backward: u_{i+1}, u_{i+2}, u_{i+3} and the tail sums T0, T1 per column; s points at row n-1
+    double2 ua[NC], ub[NC], uc[NC], T0[NC], T1[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      ua[q] = ub[q] = uc[q] = make_double2(0, 0);
+      T0[q] = T1[q] = make_double2(0, 0);
+    }
+    double vn[2 * NC], cn[5] = {0, 0, 0, 0, 0};   // right-hand side and r, u1, u2, h0, h1 of row i
+    if (n > 0) {
+#pragma unroll
+      for (int v = 0; v < 2 * NC; ++v) vn[v] = s[v * nth];
+      const double* fl = fr + (long)(n - 1) * fs;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) cn[j] = fl[(FB_R + j) * TT];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      const int k = p + 2 * i;
+      const double F0 = sF0[k + 6], F1 = sF1[k + 6];
+      double v[2 * NC];
+#pragma unroll
+      for (int j = 0; j < 2 * NC; ++j) v[j] = vn[j];
+      const double r = cn[0], u1 = cn[1], u2 = cn[2], h0 = cn[3], h1 = cn[4];
+      if (i > 0) {
+        s -= sstep;
+#pragma unroll
+        for (int j = 0; j < 2 * NC; ++j) vn[j] = s[j * nth];
+        const double* fl = fr + (long)(i - 1) * fs;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) cn[j] = fl[(FB_R + j) * TT];
+      }
+      if (i + 1 < n) {
+#pragma unroll
+        for (int q = 0; q < NC; ++q) st2<TO>(out, off[q] + (long)(i + 1) * rstep, false, ua[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        T0[q].x = fma(F0, uc[q].x, T0[q].x); T0[q].y = fma(F0, uc[q].y, T0[q].y);
+        T1[q].x = fma(F1, uc[q].x, T1[q].x); T1[q].y = fma(F1, uc[q].y, T1[q].y);
+        double2 u;
+        u.x = fma(-u1, ua[q].x, fma(-u2, ub[q].x, fma(-h0, T0[q].x, fma(-h1, T1[q].x, v[2 * q])))) * r;
+        u.y = fma(-u1, ua[q].y, fma(-u2, ub[q].y, fma(-h0, T0[q].y, fma(-h1, T1[q].y, v[2 * q + 1])))) * r;
+        uc[q] = ub[q]; ub[q] = ua[q]; ua[q] = u;
+      }
+    }
+    if (n > 0) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, off[q], false, ua[q]);
+    }
+    for (int k = nb + p; k < N; k += 2) {
+#pragma unroll
+      for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], false, make_double2(0.0, 0.0));
+    }
+  }
+}
+
 // Values per row per thread in the scratch for NC columns per thread.
 int solve_scratch_values(int basis, int nc) {
   return basis == kDirichlet ? 2 + 2 * nc : basis == kNeumann ? 3 + 2 * nc : 5 + 2 * nc;
@@ -783,15 +1196,21 @@ static size_t spread_smem(size_t need, int max_per_sm) {
   return std::max(need, cap);
 }
 
-template <typename T, int NC, typename TO>
-static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
-                            long ncols, const Wavenumbers& wn, const ColumnMap& cm, const double* tab, double* scratch,
-                            long scratch_threads, cudaStream_t s) {
+// CTAs of 128 threads for one elimination launch: one thread per work item and parity, at most
+// the scratch_threads the space's scratch holds rows for (the kernels loop over the rest).
+static unsigned solve_grid(const ColumnMap& cm, long scratch_threads) {
   const long warps_needed = 2 * ((cm.nitems + 31) / 32);
   long threads = std::min(scratch_threads, warps_needed * 32);
   threads = std::max(128L, ((threads + 127) / 128) * 128);
   threads = std::min(threads, std::max(128L, (scratch_threads / 128) * 128));
-  const unsigned grid = (unsigned)(threads / 128);
+  return (unsigned)(threads / 128);
+}
+
+template <typename T, int NC, typename TO>
+static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,
+                            long ncols, const Wavenumbers& wn, const ColumnMap& cm, const double* tab, double* scratch,
+                            long scratch_threads, cudaStream_t s) {
+  const unsigned grid = solve_grid(cm, scratch_threads);
   const int ts = N + 8;
   cudaError_t e;
   if (basis == kNeumann) {
@@ -835,6 +1254,27 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
   return cudaGetLastError();
 }
 
+// Work decomposition of a call: NC = 4 with a group table (3-D, square Fourier box), NC = 2 on
+// other 3-D spaces (pairs +l1 / -l1 along axis 1), NC = 1 on 1-D and 2-D spaces.
+static ColumnMap column_map(long ncols, const Wavenumbers& wn, const int2* groups, long ngroups, int* nc) {
+  ColumnMap cm;
+  cm.pair_m1 = 0;
+  cm.n2 = wn.n2;
+  cm.nitems = ncols;
+  cm.groups = groups;
+  *nc = 1;
+  if (wn.n1 > 1 && groups) {
+    cm.pair_m1 = wn.n1;
+    cm.nitems = ngroups;
+    *nc = 4;
+  } else if (wn.n1 > 1) {
+    cm.pair_m1 = wn.n1;
+    cm.nitems = (1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0)) * (long)wn.n2;
+    *nc = 2;
+  }
+  return cm;
+}
+
 // groups: device table of (a, b) for the four-column grouping, or nullptr; TO: type of the output
 // spectral data (T, or float for FP64 input whose solution is rounded once to FP32)
 template <typename T, typename TO>
@@ -842,23 +1282,98 @@ cudaError_t launch_solve_to(int basis, bool real, double a, double b, double c, 
                             long ncols, const Wavenumbers& wn, const double* tab, double* scratch, long scratch_threads,
                             const int2* groups, long ngroups, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
-  ColumnMap cm;
-  cm.pair_m1 = 0;
-  cm.n2 = wn.n2;
-  cm.nitems = ncols;
-  cm.groups = groups;
-  if (wn.n1 > 1 && groups) {
-    cm.pair_m1 = wn.n1;
-    cm.nitems = ngroups;
+  int nc = 1;
+  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
+  if (nc == 4)
     return solve_nc<T, 4, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
-  }
-  if (wn.n1 > 1) {  // 3-D: pair +l1 / -l1 along axis 1
-    cm.pair_m1 = wn.n1;
-    cm.nitems = (1 + (wn.n1 - 1) / 2 + (wn.n1 % 2 == 0 ? 1 : 0)) * (long)wn.n2;
+  if (nc == 2)
     return solve_nc<T, 2, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
-  }
   return solve_nc<T, 1, TO>(basis, real, a, b, c, in, out, N, ncols, wn, cm, tab, scratch, scratch_threads, s);
 }
+
+int solve_factor_values(int basis) { return basis == kDirichlet ? FD_COUNT : basis == kBiharmonic ? FB_COUNT : 0; }
+
+long solve_factor_threads(long ncols, const Wavenumbers& wn, const int2* groups, long ngroups) {
+  int nc = 1;
+  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
+  return nc == 1 ? 0 : 2 * ((cm.nitems + 31) / 32) * 32;
+}
+
+template <int NC>
+static cudaError_t factor_nc(int basis, double a, double b, double c, int N, const Wavenumbers& wn,
+                             const ColumnMap& cm, const double* tab, double* fact, cudaStream_t s) {
+  const long threads = ((2 * ((cm.nitems + 31) / 32) * 32 + 127) / 128) * 128;
+  const unsigned grid = (unsigned)std::max(1L, threads / 128);
+  const int ts = N + 8;
+  cudaError_t e;
+  if (basis == kDirichlet) {
+    const size_t smem = sizeof(double) * 2 * ts;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_factor_dirichlet<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return e;
+    k_factor_dirichlet<NC><<<grid, 128, smem, s>>>(N, a, b, wn, cm, tab, ts, fact);
+  } else {
+    const size_t smem = sizeof(double) * 13 * ts;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_factor_biharmonic<NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+      return e;
+    k_factor_biharmonic<NC><<<grid, 128, smem, s>>>(N, a, b, c, wn, cm, tab, ts, fact);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor(int basis, double a, double b, double c, int N, long ncols, const Wavenumbers& wn,
+                          const double* tab, const int2* groups, long ngroups, double* fact, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  int nc = 1;
+  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
+  if (nc != 2 || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
+  return factor_nc<2>(basis, a, b, c, N, wn, cm, tab, fact, s);
+}
+
+template <typename T, int NC, typename TO>
+static cudaError_t solve_factored_nc(int basis, const void* in, void* out, int N, long ncols,
+                                     const ColumnMap& cm, const double* tab, const double* fact, double* scratch,
+                                     long scratch_threads, cudaStream_t s) {
+  const unsigned grid = solve_grid(cm, scratch_threads);
+  const int ts = N + 8;
+  if (basis == kDirichlet) {
+    k_solve_dirichlet_f<T, NC, TO><<<grid, 128, 0, s>>>(in, out, N, ncols, cm, fact, scratch);
+  } else {
+    const size_t smem = sizeof(double) * 2 * ts;
+    cudaError_t e;
+    if (smem > 48 * 1024 &&
+        (e = cudaFuncSetAttribute(k_solve_biharmonic_f<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+      return e;
+    k_solve_biharmonic_f<T, NC, TO><<<grid, 128, smem, s>>>(in, out, N, ncols, cm, tab, ts, fact, scratch);
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, typename TO>
+cudaError_t launch_solve_factored_to(int basis, bool real, const void* in, void* out, int N, long ncols,
+                                     const Wavenumbers& wn, const double* tab, const double* fact, double* scratch,
+                                     long scratch_threads, const int2* groups, long ngroups, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  int nc = 1;
+  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
+  // 3-D spaces (complex spectral arrays), one thread per pair of columns
+  if (nc != 2 || real || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
+  return solve_factored_nc<T, 2, TO>(basis, in, out, N, ncols, cm, tab, fact, scratch, scratch_threads, s);
+}
+
+template cudaError_t launch_solve_factored_to<float, float>(int, bool, const void*, void*, int, long,
+                                                            const Wavenumbers&, const double*, const double*,
+                                                            double*, long, const int2*, long, cudaStream_t);
+template cudaError_t launch_solve_factored_to<double, double>(int, bool, const void*, void*, int, long,
+                                                              const Wavenumbers&, const double*, const double*,
+                                                              double*, long, const int2*, long, cudaStream_t);
+template cudaError_t launch_solve_factored_to<double, float>(int, bool, const void*, void*, int, long,
+                                                             const Wavenumbers&, const double*, const double*,
+                                                             double*, long, const int2*, long, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,

@@ -71,8 +71,8 @@ constexpr size_t cols_smem() {
 }
 
 // ---- Chebyshev axis, column tiles of [N][inner] ------------------------------------------------
-// MODE kChebScalar: tiles of the complex64 Fourier intermediate -> FP64 spectral array (scalar
-// product: DCT moments + Shen stencil).  MODE kChebBackward: tiles of the complex64 spectral
+// MODE kChebScalar: tiles of the complex64 Fourier intermediate -> complex64 spectral array (scalar
+// product: DCT moments + Shen stencil, both FP32; the elimination widens them exactly).  MODE kChebBackward: tiles of the complex64 spectral
 // solution -> the same array in place (Shen stencil + DCT-III); rows past the basis read as zero.
 template <int MODE, int N>
 __global__ void __launch_bounds__(kFastThreads, 2) k_cheb_stream(const __grid_constant__ CUtensorMap map,
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_cheb_stream(const __grid_co
       // v_e = x_{2e} (e < N/2), x_{2(N-1-e)+1} (e >= N/2): the even/odd reordering, read by the
       // first FFT pass in place
       fft_cols<N, kTW, kFastThreads, false>(buf, twf, [](int e) { return e < N / 2 ? 2 * e : 2 * (N - 1 - e) + 1; });
-      cheb_forward_finish<float, kChebScalar, double, N, true>(buf, nt, t0, inner, basis, 0, out, dctw);
+      cheb_forward_finish<float, kChebScalar, float, N, true>(buf, nt, t0, inner, basis, 0, out, dctw);
     } else {
       for (int idx = threadIdx.x + nb * kTW; idx < N * kTW; idx += kFastThreads) buf[idx] = make_float2(0.f, 0.f);
       __syncthreads();
@@ -341,7 +341,7 @@ bool cheb_stream_length(int N) { return N == 64 || N == 128 || N == 256; }
 bool strided_stream_length(int L) { return L == 32 || L == 64 || L == 128 || L == 256; }
 bool rows_stream_length(int LF) { return LF == 32 || LF == 64 || LF == 128 || LF == 256 || LF == 512; }
 
-// mode kChebScalar: map over the complex64 Fourier intermediate (floats), out FP64 spectral;
+// mode kChebScalar: map over the complex64 Fourier intermediate (floats), out complex64 spectral;
 // mode kChebBackward: map over the complex64 spectral solution (floats), out the same array.
 cudaError_t launch_cheb_stream(int mode, int N, const CUtensorMap& map, void* out, long inner, int basis,
                                const float2* twf, const float2* dctw, cudaStream_t s) {

@@ -16,6 +16,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fft_fast.cuh"
@@ -414,6 +415,56 @@ Wavenumbers wavenumbers(const sgm_space* s) {
   return w;
 }
 
+bool stream_capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return true;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
+// The elimination of one solve call (TI, TO: spectral input and output types).  Spaces with
+// factorisation slots (3-D Dirichlet and biharmonic) replay, one thread per pair of columns +-l1, a
+// stored factorisation of the operator
+// (a, b, c), computing it first into the least recently used slot when neither slot holds it for
+// this column layout; the factorisation kernel then runs on the caller's stream ahead of the
+// solve, so stream order keeps the slot consistent for every later call on that space.  Inside a
+// stream capture the self-contained kernels run instead, so that a captured graph never depends
+// on slot contents that later calls may replace.
+template <typename TI, typename TO>
+int eliminate(sgm_space* s, int basis, double a, double b, double c, const void* in, void* out, long ncols,
+              const Wavenumbers& wn, cudaStream_t st) {
+  const int N = (int)s->n[0];
+  if (s->fact[0] && s->fact[1] && solve_factor_values(basis) > 0 && !stream_capturing(st) &&
+      solve_factor_threads(ncols, wn, nullptr, 0) <= s->fact_threads) {
+    const double key[5] = {(double)basis, a, b, c, (double)wn.n2};
+    int slot = -1;
+    for (int i = 0; i < 2; ++i)
+      if (s->fact_valid[i] && std::memcmp(key, s->fact_key[i], sizeof key) == 0) slot = i;
+    if (slot < 0) {
+      slot = !s->fact_valid[0] ? 0 : !s->fact_valid[1] ? 1 : s->fact_use[0] <= s->fact_use[1] ? 0 : 1;
+      s->fact_valid[slot] = false;
+      SGM_TRY(wrap(launch_factor(basis, a, b, c, N, ncols, wn, s->tab, nullptr, 0, s->fact[slot], st),
+                   "factorisation"));
+      std::memcpy(s->fact_key[slot], key, sizeof key);
+      s->fact_valid[slot] = true;
+    }
+    s->fact_use[slot] = ++s->fact_clock;
+    return wrap(launch_solve_factored_to<TI, TO>(basis, s->real_spec, in, out, N, ncols, wn, s->tab, s->fact[slot],
+                                                 s->scratch, s->fact_threads, nullptr, 0, st),
+                "solve");
+  }
+  if constexpr (std::is_same<TI, TO>::value)
+    return wrap(launch_solve<TI>(basis, s->real_spec, a, b, c, in, out, N, ncols, wn, s->tab, s->scratch,
+                                 s->scratch_threads, s->groups, s->ngroups, st),
+                "solve");
+  else
+    return wrap(launch_solve_f64_to_f32(basis, a, b, c, in, out, N, ncols, wn, s->tab, s->scratch,
+                                        s->scratch_threads, s->groups, s->ngroups, st),
+                "solve");
+}
+
 template <typename T>
 int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void* in, void* out, cudaStream_t st) {
   // the Legendre kernel takes the biharmonic form a S + (b - 2 a k2) A + (a k2^2 - b k2 + c) B;
@@ -424,9 +475,7 @@ int solve_impl(sgm_space* s, int basis, double a, double b, double c, const void
   long ncols = 1;
   for (int i = 1; i < s->ndim; ++i) ncols *= s->spec[i];
   if (s->kinds[0] == SGM_SHEN_NEUMANN) basis = kNeumann;
-  return wrap(launch_solve<T>(basis, s->real_spec, a, b, c, in, out, (int)s->n[0], ncols, wavenumbers(s), s->tab,
-                              s->scratch, s->scratch_threads, s->groups, s->ngroups, st),
-              "solve");
+  return eliminate<T, T>(s, basis, a, b, c, in, out, ncols, wavenumbers(s), st);
 }
 
 // wide: write the spectral result in FP64 (FP32 spaces, internal intermediates only)
@@ -489,6 +538,8 @@ void free_space(sgm_space* s) {
   cudaFree(s->W1);
   cudaFree(s->W2);
   cudaFree(s->scratch);
+  cudaFree(s->fact[0]);
+  cudaFree(s->fact[1]);
   cudaFree(s->groups);
   for (void* p : s->tc_img) cudaFree(p);
   cudaFree(s->pdx_tab);
@@ -669,7 +720,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
   const size_t npad = s->stream ? (size_t)n[0] * s->inner_p : 0;
   const size_t wbytes = std::max({s->spec_bytes, (size_t)s->nspec * s->celem(), npad * s->celem()});
   chk(cudaMalloc(&s->W1, wbytes), "workspace");
-  // W2 holds the spectral intermediate of the physical-to-physical solves, in FP64
+  // W2 holds the spectral intermediate of the physical-to-physical solves: FP64 on the
+  // one-tile-per-CTA kernels, complex64 on the streaming pipeline
   chk(cudaMalloc(&s->W2, std::max((size_t)s->nspec, npad) * 16), "workspace");
   if (st == SGM_OK && legendre) {
     st = legendre_build(s, cheb_flags != 0 && n[0] <= kTcMaxN);
@@ -689,7 +741,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       if (ndim == 3) {
         const double L1 = s->dom[3] - s->dom[2], L2 = s->dom[5] - s->dom[4];
         const bool square = kinds[2] == SGM_FOURIER_R2C && n[1] == n[2] && std::fabs(L1 - L2) <= 1e-12 * std::fabs(L1);
-        // Four columns per factorisation leave one warp per SM sub-partition on a 256^3 box, too
+        // The self-contained eliminations (inside stream capture; the factored solves use pairs):
+        // four columns per factorisation leave one warp per SM sub-partition on a 256^3 box, too
         // few to hide the latency of dependent FP64 instructions; the Dirichlet elimination, whose
         // per-column work is small next to its factorisation, runs faster with pairs and twice the
         // warps.  The biharmonic elimination keeps the groups of four.
@@ -718,7 +771,27 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
                                           : kinds[0] == SGM_SHEN_NEUMANN ? kNeumann
                                                                          : kBiharmonic,
                                           s->solve_nc);
-      chk(cudaMalloc(&s->scratch, sizeof(double) * rows * nv * s->scratch_threads), "solve scratch");
+      size_t scratch_bytes = sizeof(double) * rows * nv * s->scratch_threads;
+      // factorisation slots of the 3-D Dirichlet and biharmonic eliminations.  The factored solves
+      // run one thread per pair of columns +-l1 (twice the warps of the four-column groups, which
+      // pay off only while the factorisation is recomputed), for either column layout (spectral
+      // arrays; the padded streaming intermediates); their scratch holds 2 x 2 values per row
+      const int nvf = kinds[0] == SGM_SHEN_DIRICHLET ? solve_factor_values(kDirichlet)
+                      : kinds[0] == SGM_SHEN_BIHARMONIC ? solve_factor_values(kBiharmonic)
+                                                        : 0;
+      if (st == SGM_OK && ndim == 3 && nvf > 0) {
+        Wavenumbers wn = wavenumbers(s);
+        long thr = solve_factor_threads(s->nspec / N, wn, nullptr, 0);
+        if (s->stream) {
+          wn.n2 = s->hp;
+          thr = std::max(thr, solve_factor_threads(s->inner_p, wn, nullptr, 0));
+        }
+        s->fact_threads = ((thr + 127) / 128) * 128;
+        scratch_bytes = std::max(scratch_bytes, sizeof(double) * rows * 4 * s->fact_threads);
+        for (int i = 0; i < 2 && st == SGM_OK; ++i)
+          chk(cudaMalloc(&s->fact[i], sizeof(double) * rows * nvf * s->fact_threads), "factorisation table");
+      }
+      chk(cudaMalloc(&s->scratch, scratch_bytes), "solve scratch");
     }
   }
   if (st == SGM_OK && cheb && cheb_flags && n[0] <= kTcMaxN) {
@@ -864,9 +937,10 @@ int sgm_biharmonic_solve(sgm_space* s, double a, double b, double c, const void*
 }
 
 // Physical -> physical on the streaming pipeline (FP32 spaces, see sgm_space::stream): R2C rows
-// into the padded W1, the strided C2C axis in place, the Chebyshev scalar product into the padded
-// FP64 W2, the FP64 solve from W2 with its result rounded once into W1 (the padding columns are
-// solved as dummy columns), and the Chebyshev, strided and C2R passes backwards from W1.
+// into the padded W1, the strided C2C axis in place, the Chebyshev scalar product (FP32 moments and
+// stencil) into the padded W2 as complex64, the FP64 solve from W2 (inputs widened exactly, the
+// result rounded once into W1; the padding columns are solved as dummy columns), and the Chebyshev,
+// strided and C2R passes backwards from W1.
 static int stream_entry(sgm_space* s, int basis, double a, double b, double c, const void* f, void* u,
                         cudaStream_t st) {
   const int nd = s->ndim;
@@ -892,9 +966,7 @@ static int stream_entry(sgm_space* s, int basis, double a, double b, double c, c
   wn.n2 = s->hp;
   if (s->kinds[0] == SGM_SHEN_NEUMANN) basis = kNeumann;
   if (s->ev_solve_begin) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_begin, st), "solve event"));
-  SGM_TRY(wrap(launch_solve_f64_to_f32(basis, a, b, c, s->W2, w1, N0, s->inner_p, wn, s->tab, s->scratch,
-                                       s->scratch_threads, s->groups, s->ngroups, st),
-               "solve"));
+  SGM_TRY((eliminate<float, float>(s, basis, a, b, c, s->W2, w1, s->inner_p, wn, st)));
   if (s->ev_solve_end) SGM_TRY(wrap(cudaEventRecord(s->ev_solve_end, st), "solve event"));
   SGM_TRY(wrap(launch_cheb_stream(kChebBackward, N0, s->map_w1, w1, s->inner_p, s->kinds[0], (const float2*)twN,
                                   (const float2*)s->dctw, st),

@@ -32,9 +32,19 @@ struct sgm_space {
   void* W2 = nullptr;
   double* scratch = nullptr;
   long scratch_threads = 0;
-  int2* groups = nullptr;    // (a, b) table of the four-column grouping of the eliminations
+  int2* groups = nullptr;    // (a, b) table of the four-column grouping of the self-contained eliminations
   long ngroups = 0;
   int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
+  // factorisation tables of the 3-D Dirichlet and biharmonic eliminations (k_solve.cu
+  // launch_factor, pairs of columns): two slots of rows x values x fact_threads doubles, each keyed
+  // by the operator and column layout it holds (basis, a, b, c, n2) and replaced least recently
+  // used; the scratch holds the factored solves' rows for fact_threads threads
+  double* fact[2] = {nullptr, nullptr};
+  double fact_key[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
+  bool fact_valid[2] = {false, false};
+  unsigned long fact_use[2] = {0, 0};
+  unsigned long fact_clock = 0;
+  long fact_threads = 0;
   int cheb_tc = 0;           // 1: Chebyshev axis by the tensor-core contraction (k_cheb_tc.cu)
   void* tc_img[3] = {nullptr, nullptr, nullptr};  // contraction matrices per ChebMode
   void* pdx_tab = nullptr;   // Shen-to-Chebyshev stencil coefficients of sgm_project_dx (project.cu)
@@ -42,8 +52,8 @@ struct sgm_space {
   double* leg_band = nullptr;   // band entries of the Legendre Galerkin matrices, 6 per basis row
   double* leg_scratch = nullptr;
   long leg_threads = 0;
-  // streaming pipeline of the physical-to-physical solves on FP32 spaces (k_stream.cu): W1
-  // (complex64) and W2 (FP64) hold the intermediates with the last axis padded to hp (even)
+  // streaming pipeline of the physical-to-physical solves on FP32 spaces (k_stream.cu): W1 and W2
+  // (both complex64) hold the intermediates with the last axis padded to hp (even)
   // coefficients per row, so every row starts on a 16-byte boundary; TMA tensor maps over W1 for
   // the Chebyshev passes (as floats, 2-D) and the strided passes (3-D)
   // a space whose axes are not in the canonical order (axes.cu) is a view of the canonical space
@@ -90,7 +100,7 @@ int build_project_table(sgm_space* s);
 // of type TS (float or double)
 int legendre_build(sgm_space* s, bool tc_images);
 // streaming passes (k_stream.cu): lengths with a kernel, the launches (Chebyshev mode
-// kChebScalar: map over the complex64 intermediate, FP64 spectral out; kChebBackward: map over
+// kChebScalar: map over the complex64 intermediate, complex64 spectral out; kChebBackward: map over
 // the complex64 spectral solution, transformed in place) and the tensor-map encoder (tma.cuh)
 bool cheb_stream_length(int N);
 cudaError_t launch_cheb_stream(int mode, int N, const CUtensorMap& map, void* out, long inner, int basis,
