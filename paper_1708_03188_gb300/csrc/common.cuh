@@ -143,16 +143,15 @@ cudaError_t launch_solve_f64_to_f32(int basis, double a, double b, double c, con
 // factorisation table (0: the basis has none), work threads of the table for a call's column
 // layout (0: a 1-D or 2-D space, no factored form), the factorisation of the operator (a, b, c)
 // into a table of rows x values x threads doubles, and the solve replaying a table (TI, TO:
-// spectral input and output types; the table must come from launch_factor with the same
-// basis, N, columns and wavenumbers).  The factored forms take one thread per pair of columns of a
-// 3-D space: groups must be null.
+// spectral input and output types; the table must come from launch_factor with the same basis, N,
+// columns and wavenumbers; scratch_threads: threads the scratch holds 2 doubles per row for).
 int solve_factor_values(int basis);
-long solve_factor_threads(long ncols, const Wavenumbers& wn, const int2* groups, long ngroups);
+long solve_factor_threads(long ncols, const Wavenumbers& wn);
 cudaError_t launch_factor(int basis, double a, double b, double c, int N, long ncols, const Wavenumbers& wn,
-                          const double* tab, const int2* groups, long ngroups, double* fact, cudaStream_t s);
+                          const double* tab, double* fact, cudaStream_t s);
 template <typename TI, typename TO>
 cudaError_t launch_solve_factored_to(int basis, bool real, const void* in, void* out, int N, long ncols,
                                      const Wavenumbers& wn, const double* tab, const double* fact, double* scratch,
-                                     long scratch_threads, const int2* groups, long ngroups, cudaStream_t s);
+                                     long scratch_threads, cudaStream_t s);
 
 }  // namespace sgm

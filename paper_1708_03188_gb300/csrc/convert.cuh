@@ -2,8 +2,9 @@
 //
 // On GB300 the FP64 pipe executes 2 operations per clock per SM and the hardware
 // float<->double conversions issue on it, so the FP64 eliminations of k_solve.cu do these
-// conversions with integer bit operations (IEEE 754 binary32/binary64 layouts) and fall
-// back to the hardware instruction only for zeros, subnormals, infinities and NaNs.
+// conversions with integer bit operations (IEEE 754 binary32/binary64 layouts).  Widening
+// never uses the hardware conversion; narrowing falls back to it for results outside the
+// normal FP32 range (zeros, subnormals, overflow) and for non-finite inputs.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -12,14 +13,24 @@
 namespace sgm {
 
 // Exact widening: binary32 exponent e (bias 127) -> e + 896 (bias 1023); the 23-bit
-// significand moves to the top of the 52-bit field.
+// significand moves to the top of the 52-bit field.  Every class stays on the integer pipe: zero
+// keeps exponent 0; a subnormal significand m is normalised (the shift sh = clz(m) - 8 brings its
+// leading one to bit 23, and the value m 2^-149 has binary64 exponent 897 - sh); infinities and NaNs
+// keep the all-ones exponent.
 __device__ __forceinline__ double widen_f32(float f) {
   const unsigned b = __float_as_uint(f);
   const unsigned e = (b >> 23) & 0xffu;
-  if (e == 0u || e == 0xffu) return (double)f;
-  const unsigned hi = (b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3);
-  const unsigned lo = b << 29;
-  return __hiloint2double((int)hi, (int)lo);
+  const unsigned m = b & 0x7fffffu;
+  const unsigned sh = __clz(m) - 8u;
+  unsigned E = e + 896u, M = m;
+  if (e == 0u) {
+    E = m == 0u ? 0u : 897u - sh;
+    M = m == 0u ? 0u : (m << sh) & 0x7fffffu;
+  } else if (e == 0xffu) {
+    E = 0x7ffu;
+  }
+  const unsigned hi = (b & 0x80000000u) | (E << 20) | (M >> 3);
+  return __hiloint2double((int)hi, (int)(M << 29));
 }
 
 // Round to nearest, ties to even: keep the top 23 of the 52 significand bits and add one

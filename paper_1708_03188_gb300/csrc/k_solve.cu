@@ -25,7 +25,8 @@
 //   right]; each row eliminates its two sub-diagonal entries against the two reduced rows
 //   above it.
 //
-// Work decomposition.  On a 3-D space the columns with Fourier indices (l1, l2) and
+// Work decomposition of the self-contained kernels below (the factored solves of 3-D spaces, further
+// down, take one column per thread).  On a 3-D space the columns with Fourier indices (l1, l2) and
 // (-l1, l2) have the same kappa2 and hence the same matrix, so one thread eliminates the
 // pair (NC = 2): the FP64 factorisation (pivots, reciprocals, tail coefficients) is shared
 // and only the right-hand-side recurrences are done per column.  Columns l1 = 0 and
@@ -65,6 +66,20 @@ __device__ __forceinline__ double rcp64(double x) {
 template <typename T> __device__ __forceinline__ double2 ld2(const void* p, long i, bool real) {
   if (real) return make_double2(widen<T>(reinterpret_cast<const T*>(p)[i]), 0.0);
   const cplx<T> v = reinterpret_cast<const cplx<T>*>(p)[i];
+  return make_double2(widen<T>(v.x), widen<T>(v.y));
+}
+// The element as stored (real arrays: imaginary part zero), for loads issued ahead of their use:
+// widening at the load would make the warp wait for the load right there.
+template <typename T> __device__ __forceinline__ cplx<T> ldraw(const void* p, long i, bool real) {
+  if (real) {
+    cplx<T> v;
+    v.x = reinterpret_cast<const T*>(p)[i];
+    v.y = T(0);
+    return v;
+  }
+  return reinterpret_cast<const cplx<T>*>(p)[i];
+}
+template <typename T> __device__ __forceinline__ double2 widen2(const cplx<T>& v) {
   return make_double2(widen<T>(v.x), widen<T>(v.y));
 }
 template <typename T> __device__ __forceinline__ void st2(void* p, long i, bool real, double2 v) {
@@ -156,9 +171,10 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
 #pragma unroll
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
     const long rstep = 2 * ncols;
-    double2 fn[NC];   // right-hand side of the next row, loaded one row ahead
+    cplx<T> fn[NC];   // right-hand side of the next row, loaded one row ahead (widened when used)
 #pragma unroll
-    for (int q = 0; q < NC; ++q) fn[q] = n > 0 ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+    for (int q = 0; q < NC; ++q)
+      if (n > 0) fn[q] = ldraw<T>(in, off[q], real);
     double* s = scratch + gt;
     const long sstep = (long)NV * nth;
     for (int i = 0; i < n; ++i) {
@@ -166,8 +182,8 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
       double2 f[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        f[q] = fn[q];
-        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+        f[q] = widen2<T>(fn[q]);
+        if (i + 1 < n) fn[q] = ldraw<T>(in, off[q] + (long)(i + 1) * rstep, real);
       }
       double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
       double g = aG[k];
@@ -203,7 +219,6 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet(const void* __restrict_
       for (int v = 0; v < NV; ++v) vn[v] = s[v * nth];
     }
     for (int i = n - 1; i >= 0; --i) {
-      const int k = p + 2 * i;
       double v[NV];
 #pragma unroll
       for (int j = 0; j < NV; ++j) v[j] = vn[j];
@@ -428,19 +443,20 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
     for (int q = 0; q < NC; ++q) fl[q] = make_double2(0.0, 0.0);
     if (side == 0) {
       double pr = 0.0, pge = 0.0, pg = 0.0;
-      double2 pf[NC], fn[NC];
+      double2 pf[NC];
+      cplx<T> fn[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         pf[q] = make_double2(0.0, 0.0);
-        fn[q] = (valid && h > 0) ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+        if (valid && h > 0) fn[q] = ldraw<T>(in, off[q], real);
       }
       for (int i = 0; i < h; ++i) {
         const int k = p + 2 * i;
         double2 f[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          f[q] = fn[q];
-          if (valid && i + 1 < h) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+          f[q] = (valid && h > 0) ? widen2<T>(fn[q]) : make_double2(0.0, 0.0);
+          if (valid && i + 1 < h) fn[q] = ldraw<T>(in, off[q] + (long)(i + 1) * rstep, real);
         }
         double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
         double g = aG[k];
@@ -471,19 +487,20 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
       for (int q = 0; q < NC; ++q) fl[q] = pf[q];
     } else {
       double bn = 0.0, Bn = 0.0;
-      double2 an[NC], An[NC], fn[NC];
+      double2 an[NC], An[NC];
+      cplx<T> fn[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
         an[q] = An[q] = make_double2(0.0, 0.0);
-        fn[q] = (valid && n > h) ? ld2<T>(in, off[q] + (long)(n - 1) * rstep, real) : make_double2(0.0, 0.0);
+        if (valid && n > h) fn[q] = ldraw<T>(in, off[q] + (long)(n - 1) * rstep, real);
       }
       for (int i = n - 1; i >= h; --i) {
         const int k = p + 2 * i;
         double2 f[NC];
 #pragma unroll
         for (int q = 0; q < NC; ++q) {
-          f[q] = fn[q];
-          if (valid && i - 1 >= h) fn[q] = ld2<T>(in, off[q] + (long)(i - 1) * rstep, real);
+          f[q] = valid ? widen2<T>(fn[q]) : make_double2(0.0, 0.0);
+          if (valid && i - 1 >= h) fn[q] = ldraw<T>(in, off[q] + (long)(i - 1) * rstep, real);
         }
         const double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
         const double g = aG[k];
@@ -649,9 +666,10 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
 #pragma unroll
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
     const long rstep = 2 * ncols;
-    double2 fn[NC];   // right-hand side of the next row, loaded one row ahead
+    cplx<T> fn[NC];   // right-hand side of the next row, loaded one row ahead (widened when used)
 #pragma unroll
-    for (int q = 0; q < NC; ++q) fn[q] = n > 0 ? ld2<T>(in, off[q], real) : make_double2(0.0, 0.0);
+    for (int q = 0; q < NC; ++q)
+      if (n > 0) fn[q] = ldraw<T>(in, off[q], real);
     double* s = scratch + gt;
     const long sstep = (long)NV * nth;
     for (int i = 0; i < n; ++i) {
@@ -659,8 +677,8 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
       double2 f[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        f[q] = fn[q];
-        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, real);
+        f[q] = widen2<T>(fn[q]);
+        if (i + 1 < n) fn[q] = ldraw<T>(in, off[q] + (long)(i + 1) * rstep, real);
       }
       const double q4 = aB * tb(SB4, k);
       double D = fma(aA, tb(SA0, k), fma(aB, tb(SB0, k), tb(SS0, k)));
@@ -771,10 +789,12 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
 // k_factor_* runs the top-down factorisation of the kernels above and stores it per work item in
 // a table laid out [row][value][work thread] (work thread = 32 * warp + lane of the work
 // decomposition above, so a warp reads 256 contiguous bytes per value); k_solve_*_f replays only
-// the right-hand-side recurrences from the table.  Both use one thread per pair of columns +-l1
-// (NC = 2): without the factorisation to share, four columns per thread would only halve the warps
-// that hide the FP64 latency.  FP64 operations per row and complex column: Dirichlet 10 (against 16
-// with the factorisation shared by a pair), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal pivots are the same FP64
+// the right-hand-side recurrences from the table.  Both run one thread per column and parity
+// (NC = 1): with no factorisation left to share between the columns of a thread, single columns
+// give four times the warps of the four-column groups, to hide the FP64 latency and to share the
+// SMs with a concurrent solve's kernels in small, even units (and a quarter of the registers).
+// FP64 operations per row and complex column: Dirichlet 10 (against 16 with the factorisation
+// shared by a pair of columns), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal pivots are the same FP64
 // values the kernels above compute; the back substitution adds the term of the unknown just
 // solved last, so that its dependent chain is one FMA and one multiply per row.
 enum { FD_MU = 0, FD_R, FD_G, FD_GE, FD_COUNT };                        // Dirichlet table values
@@ -862,11 +882,14 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet_f(const void* __restric
 #pragma unroll
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
     const long rstep = 2 * ncols;
-    // forward: f'_i = f_i - mu_i f'_{i-1} into the scratch; operands loaded one row ahead
-    double2 fn[NC], pf[NC];
+    // forward: f'_i = f_i - mu_i f'_{i-1} into the scratch; operands loaded one row ahead and
+    // kept as loaded (widened when used, so that the load's latency stays hidden)
+    const cplx<T>* src = reinterpret_cast<const cplx<T>*>(in);
+    cplx<T> fn[NC];
+    double2 pf[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      fn[q] = n > 0 ? ld2<T>(in, off[q], false) : make_double2(0.0, 0.0);
+      if (n > 0) fn[q] = src[off[q]];
       pf[q] = make_double2(0.0, 0.0);
     }
     double mun = n > 0 ? fr[FD_MU * TT] : 0.0;
@@ -877,8 +900,8 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet_f(const void* __restric
       double2 f[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        f[q] = fn[q];
-        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, false);
+        f[q] = widen2<T>(fn[q]);
+        if (i + 1 < n) fn[q] = src[off[q] + (long)(i + 1) * rstep];
       }
       if (i + 1 < n) mun = fr[(long)(i + 1) * fs + FD_MU * TT];
       if (i > 0) {   // row i - 1
@@ -1074,11 +1097,14 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
     const long rstep = 2 * ncols;
     // forward: f'_i = f_i - mu_i f'_{i-2} - mu1_i f'_{i-1} (the multipliers are zero where the
-    // rows above do not exist); operands loaded one row ahead, each row stored one row late
-    double2 fn[NC], f1[NC], f2[NC];
+    // rows above do not exist); operands loaded one row ahead as loaded (widened when used), each
+    // row stored one row late
+    const cplx<T>* src = reinterpret_cast<const cplx<T>*>(in);
+    cplx<T> fn[NC];
+    double2 f1[NC], f2[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) {
-      fn[q] = n > 0 ? ld2<T>(in, off[q], false) : make_double2(0.0, 0.0);
+      if (n > 0) fn[q] = src[off[q]];
       f1[q] = f2[q] = make_double2(0.0, 0.0);
     }
     double mun = 0.0, mu1n = 0.0;
@@ -1090,8 +1116,8 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
       double2 f[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q) {
-        f[q] = fn[q];
-        if (i + 1 < n) fn[q] = ld2<T>(in, off[q] + (long)(i + 1) * rstep, false);
+        f[q] = widen2<T>(fn[q]);
+        if (i + 1 < n) fn[q] = src[off[q] + (long)(i + 1) * rstep];
       }
       if (i + 1 < n) {
         const double* fl = fr + (long)(i + 1) * fs;
@@ -1136,9 +1162,10 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
 #pragma unroll
       for (int j = 0; j < 5; ++j) cn[j] = fl[(FB_R + j) * TT];
     }
+    // tail weights of row i (k = p + 2i) at k + 6, read one row ahead like the rest
+    double F0n = n > 0 ? sF0[p + 2 * (n - 1) + 6] : 0.0, F1n = n > 0 ? sF1[p + 2 * (n - 1) + 6] : 0.0;
     for (int i = n - 1; i >= 0; --i) {
-      const int k = p + 2 * i;
-      const double F0 = sF0[k + 6], F1 = sF1[k + 6];
+      const double F0 = F0n, F1 = F1n;
       double v[2 * NC];
 #pragma unroll
       for (int j = 0; j < 2 * NC; ++j) v[j] = vn[j];
@@ -1150,6 +1177,8 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
         const double* fl = fr + (long)(i - 1) * fs;
 #pragma unroll
         for (int j = 0; j < 5; ++j) cn[j] = fl[(FB_R + j) * TT];
+        F0n = sF0[p + 2 * (i - 1) + 6];
+        F1n = sF1[p + 2 * (i - 1) + 6];
       }
       if (i + 1 < n) {
 #pragma unroll
@@ -1293,10 +1322,21 @@ cudaError_t launch_solve_to(int basis, bool real, double a, double b, double c, 
 
 int solve_factor_values(int basis) { return basis == kDirichlet ? FD_COUNT : basis == kBiharmonic ? FB_COUNT : 0; }
 
-long solve_factor_threads(long ncols, const Wavenumbers& wn, const int2* groups, long ngroups) {
-  int nc = 1;
-  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
-  return nc == 1 ? 0 : 2 * ((cm.nitems + 31) / 32) * 32;
+// Work decomposition of the factored solves of 3-D spaces: one thread per column and parity.
+static ColumnMap factored_map(long ncols, const Wavenumbers& wn, bool* ok) {
+  ColumnMap cm;
+  cm.pair_m1 = 0;
+  cm.n2 = wn.n2;
+  cm.nitems = ncols;
+  cm.groups = nullptr;
+  *ok = wn.n1 > 1;   // 1-D and 2-D spaces have no factored form
+  return cm;
+}
+
+long solve_factor_threads(long ncols, const Wavenumbers& wn) {
+  bool ok = false;
+  const ColumnMap cm = factored_map(ncols, wn, &ok);
+  return ok ? 2 * ((cm.nitems + 31) / 32) * 32 : 0;
 }
 
 template <int NC>
@@ -1325,12 +1365,12 @@ static cudaError_t factor_nc(int basis, double a, double b, double c, int N, con
 }
 
 cudaError_t launch_factor(int basis, double a, double b, double c, int N, long ncols, const Wavenumbers& wn,
-                          const double* tab, const int2* groups, long ngroups, double* fact, cudaStream_t s) {
+                          const double* tab, double* fact, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
-  int nc = 1;
-  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
-  if (nc != 2 || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
-  return factor_nc<2>(basis, a, b, c, N, wn, cm, tab, fact, s);
+  bool ok = false;
+  const ColumnMap cm = factored_map(ncols, wn, &ok);
+  if (!ok || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
+  return factor_nc<1>(basis, a, b, c, N, wn, cm, tab, fact, s);
 }
 
 template <typename T, int NC, typename TO>
@@ -1356,24 +1396,24 @@ static cudaError_t solve_factored_nc(int basis, const void* in, void* out, int N
 template <typename T, typename TO>
 cudaError_t launch_solve_factored_to(int basis, bool real, const void* in, void* out, int N, long ncols,
                                      const Wavenumbers& wn, const double* tab, const double* fact, double* scratch,
-                                     long scratch_threads, const int2* groups, long ngroups, cudaStream_t s) {
+                                     long scratch_threads, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
-  int nc = 1;
-  const ColumnMap cm = column_map(ncols, wn, groups, ngroups, &nc);
-  // 3-D spaces (complex spectral arrays), one thread per pair of columns
-  if (nc != 2 || real || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
-  return solve_factored_nc<T, 2, TO>(basis, in, out, N, ncols, cm, tab, fact, scratch, scratch_threads, s);
+  bool ok = false;
+  const ColumnMap cm = factored_map(ncols, wn, &ok);
+  // 3-D spaces (complex spectral arrays)
+  if (!ok || real || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
+  return solve_factored_nc<T, 1, TO>(basis, in, out, N, ncols, cm, tab, fact, scratch, scratch_threads, s);
 }
 
 template cudaError_t launch_solve_factored_to<float, float>(int, bool, const void*, void*, int, long,
                                                             const Wavenumbers&, const double*, const double*,
-                                                            double*, long, const int2*, long, cudaStream_t);
+                                                            double*, long, cudaStream_t);
 template cudaError_t launch_solve_factored_to<double, double>(int, bool, const void*, void*, int, long,
                                                               const Wavenumbers&, const double*, const double*,
-                                                              double*, long, const int2*, long, cudaStream_t);
+                                                              double*, long, cudaStream_t);
 template cudaError_t launch_solve_factored_to<double, float>(int, bool, const void*, void*, int, long,
                                                              const Wavenumbers&, const double*, const double*,
-                                                             double*, long, const int2*, long, cudaStream_t);
+                                                             double*, long, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_solve(int basis, bool real, double a, double b, double c, const void* in, void* out, int N,

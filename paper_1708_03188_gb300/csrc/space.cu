@@ -425,7 +425,7 @@ bool stream_capturing(cudaStream_t st) {
 }
 
 // The elimination of one solve call (TI, TO: spectral input and output types).  Spaces with
-// factorisation slots (3-D Dirichlet and biharmonic) replay, one thread per pair of columns +-l1, a
+// factorisation slots (3-D Dirichlet and biharmonic) replay, one thread per column and parity, a
 // stored factorisation of the operator
 // (a, b, c), computing it first into the least recently used slot when neither slot holds it for
 // this column layout; the factorisation kernel then runs on the caller's stream ahead of the
@@ -437,7 +437,7 @@ int eliminate(sgm_space* s, int basis, double a, double b, double c, const void*
               const Wavenumbers& wn, cudaStream_t st) {
   const int N = (int)s->n[0];
   if (s->fact[0] && s->fact[1] && solve_factor_values(basis) > 0 && !stream_capturing(st) &&
-      solve_factor_threads(ncols, wn, nullptr, 0) <= s->fact_threads) {
+      solve_factor_threads(ncols, wn) <= s->fact_threads) {
     const double key[5] = {(double)basis, a, b, c, (double)wn.n2};
     int slot = -1;
     for (int i = 0; i < 2; ++i)
@@ -445,14 +445,13 @@ int eliminate(sgm_space* s, int basis, double a, double b, double c, const void*
     if (slot < 0) {
       slot = !s->fact_valid[0] ? 0 : !s->fact_valid[1] ? 1 : s->fact_use[0] <= s->fact_use[1] ? 0 : 1;
       s->fact_valid[slot] = false;
-      SGM_TRY(wrap(launch_factor(basis, a, b, c, N, ncols, wn, s->tab, nullptr, 0, s->fact[slot], st),
-                   "factorisation"));
+      SGM_TRY(wrap(launch_factor(basis, a, b, c, N, ncols, wn, s->tab, s->fact[slot], st), "factorisation"));
       std::memcpy(s->fact_key[slot], key, sizeof key);
       s->fact_valid[slot] = true;
     }
     s->fact_use[slot] = ++s->fact_clock;
     return wrap(launch_solve_factored_to<TI, TO>(basis, s->real_spec, in, out, N, ncols, wn, s->tab, s->fact[slot],
-                                                 s->scratch, s->fact_threads, nullptr, 0, st),
+                                                 s->scratch, s->fact_threads, st),
                 "solve");
   }
   if constexpr (std::is_same<TI, TO>::value)
@@ -741,7 +740,8 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       if (ndim == 3) {
         const double L1 = s->dom[3] - s->dom[2], L2 = s->dom[5] - s->dom[4];
         const bool square = kinds[2] == SGM_FOURIER_R2C && n[1] == n[2] && std::fabs(L1 - L2) <= 1e-12 * std::fabs(L1);
-        // The self-contained eliminations (inside stream capture; the factored solves use pairs):
+        // The self-contained eliminations (inside stream capture; the factored solves take one
+        // column per thread):
         // four columns per factorisation leave one warp per SM sub-partition on a 256^3 box, too
         // few to hide the latency of dependent FP64 instructions; the Dirichlet elimination, whose
         // per-column work is small next to its factorisation, runs faster with pairs and twice the
@@ -773,21 +773,21 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
                                           s->solve_nc);
       size_t scratch_bytes = sizeof(double) * rows * nv * s->scratch_threads;
       // factorisation slots of the 3-D Dirichlet and biharmonic eliminations.  The factored solves
-      // run one thread per pair of columns +-l1 (twice the warps of the four-column groups, which
-      // pay off only while the factorisation is recomputed), for either column layout (spectral
-      // arrays; the padded streaming intermediates); their scratch holds 2 x 2 values per row
+      // run one thread per column and parity (the four-column groups pay off only while the
+      // factorisation is recomputed), for either column layout (spectral arrays; the padded
+      // streaming intermediates); their scratch holds 2 values per row and thread
       const int nvf = kinds[0] == SGM_SHEN_DIRICHLET ? solve_factor_values(kDirichlet)
                       : kinds[0] == SGM_SHEN_BIHARMONIC ? solve_factor_values(kBiharmonic)
                                                         : 0;
       if (st == SGM_OK && ndim == 3 && nvf > 0) {
         Wavenumbers wn = wavenumbers(s);
-        long thr = solve_factor_threads(s->nspec / N, wn, nullptr, 0);
+        long thr = solve_factor_threads(s->nspec / N, wn);
         if (s->stream) {
           wn.n2 = s->hp;
-          thr = std::max(thr, solve_factor_threads(s->inner_p, wn, nullptr, 0));
+          thr = std::max(thr, solve_factor_threads(s->inner_p, wn));
         }
         s->fact_threads = ((thr + 127) / 128) * 128;
-        scratch_bytes = std::max(scratch_bytes, sizeof(double) * rows * 4 * s->fact_threads);
+        scratch_bytes = std::max(scratch_bytes, sizeof(double) * rows * 2 * s->fact_threads);
         for (int i = 0; i < 2 && st == SGM_OK; ++i)
           chk(cudaMalloc(&s->fact[i], sizeof(double) * rows * nvf * s->fact_threads), "factorisation table");
       }

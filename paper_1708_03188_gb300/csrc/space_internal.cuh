@@ -36,9 +36,10 @@ struct sgm_space {
   long ngroups = 0;
   int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
   // factorisation tables of the 3-D Dirichlet and biharmonic eliminations (k_solve.cu
-  // launch_factor, pairs of columns): two slots of rows x values x fact_threads doubles, each keyed
-  // by the operator and column layout it holds (basis, a, b, c, n2) and replaced least recently
-  // used; the scratch holds the factored solves' rows for fact_threads threads
+  // launch_factor, one thread per column and parity): two slots of rows x values x fact_threads
+  // doubles, each keyed by the operator and column layout it holds (basis, a, b, c, n2) and
+  // replaced least recently used; the scratch holds the factored solves' rows for fact_threads
+  // threads
   double* fact[2] = {nullptr, nullptr};
   double fact_key[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
   bool fact_valid[2] = {false, false};
