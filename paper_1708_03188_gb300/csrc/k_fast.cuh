@@ -148,6 +148,25 @@ __global__ void __launch_bounds__(kFastThreads) k_strided_fast(const cplx<T>* in
 template <typename T> __device__ __forceinline__ T fbeta(int k) { return (T)(-2 * (k + 2)) / (T)(k + 3); }
 template <typename T> __device__ __forceinline__ T fgamma(int k) { return (T)(k + 1) / (T)(k + 3); }
 
+// Per-row tables of a Chebyshev pass held in shared memory by a persistent CTA (k_stream.cu):
+// the DCT twiddles exp(-i pi k / (2N)) and the Shen stencil coefficients (c1 = beta_k for the
+// biharmonic basis, q_k for the Neumann basis; c2 = gamma_k), so that the per-element work reads
+// them instead of computing divisions or loading through the texture path.  A null table means:
+// compute the coefficients and read the twiddles from global memory.
+template <typename T> struct ChebTables {
+  const cplx<T>* dctw;   // shared
+  const T* c1;           // shared
+  const T* c2;           // shared
+};
+template <typename T> __device__ __forceinline__ void fill_cheb_tables(cplx<T>* dctw_s, T* c1, T* c2, int N, int basis,
+                                                                       const cplx<T>* __restrict__ dctw) {
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    dctw_s[k] = __ldg(&dctw[k]);
+    c1[k] = basis == kBiharmonic ? fbeta<T>(k) : basis == kNeumann ? neumann_q<T>(k) : (T)0;
+    c2[k] = basis == kBiharmonic ? fgamma<T>(k) : (T)0;
+  }
+}
+
 // position of input point j in the even/odd (Makhoul) reordering of a length-N line
 template <int N> __device__ __forceinline__ int cheb_reord(int j) { return (j & 1) ? N - 1 - (j >> 1) : (j >> 1); }
 
@@ -164,7 +183,8 @@ template <bool COLS, int N, int TW> struct TileIdx {
 // then the Shen stencil of `basis`, written to `out` at rows k, columns t0 + t (t < nt).
 template <typename T, int MODE, typename TS, int N, bool COLS = false>
 __device__ __forceinline__ void cheb_forward_finish(cplx<T>* buf, int nt, long t0, long inner, int basis, int real,
-                                                    void* __restrict__ out, const cplx<T>* __restrict__ dctw) {
+                                                    void* __restrict__ out, const cplx<T>* __restrict__ dctw,
+                                                    const ChebTables<T>* tabs = nullptr) {
   using C = cplx<T>;
   constexpr int TW = fast_tw_cols<T>();
   using I = TileIdx<COLS, N, TW>;
@@ -180,7 +200,7 @@ __device__ __forceinline__ void cheb_forward_finish(cplx<T>* buf, int nt, long t
     if (t < nt) {
       const C v = buf[I::at(t, k)];
       const C vr = cconj(buf[I::at(t, k == 0 ? 0 : N - k)]);
-      const C w = __ldg(&dctw[k]);
+      const C w = tabs ? tabs->dctw[k] : __ldg(&dctw[k]);
       const C a = cadd(v, vr), b = csub(v, vr);
       T sc = scale;
       if (MODE == kChebForwardT && k == 0) sc *= (T)0.5;
@@ -205,11 +225,11 @@ __device__ __forceinline__ void cheb_forward_finish(cplx<T>* buf, int nt, long t
       } else if (basis == kDirichlet) {
         s = csub(buf[I::at(t, k)], buf[I::at(t, k + 2)]);
       } else if (basis == kNeumann) {
-        const T q = neumann_q<T>(k);
+        const T q = tabs ? tabs->c1[k] : neumann_q<T>(k);
         const C a0 = buf[I::at(t, k)], a2 = buf[I::at(t, k + 2)];
         s = mk<C>(a0.x - q * a2.x, a0.y - q * a2.y);
       } else {
-        const T be = fbeta<T>(k), ga = fgamma<T>(k);
+        const T be = tabs ? tabs->c1[k] : fbeta<T>(k), ga = tabs ? tabs->c2[k] : fgamma<T>(k);
         const C a0 = buf[I::at(t, k)], a2 = buf[I::at(t, k + 2)], a4 = buf[I::at(t, k + 4)];
         s = mk<C>(a0.x + be * a2.x + ga * a4.x, a0.y + be * a2.y + ga * a4.y);
       }

@@ -69,6 +69,71 @@ template <int L>
 constexpr size_t cols_smem() {
   return (size_t)kStages * L * kTW * sizeof(float2) + kStages * sizeof(uint64_t);
 }
+// the Chebyshev kernels add the per-row tables (DCT twiddles, two stencil coefficients)
+template <int N>
+constexpr size_t cheb_smem() {
+  return cols_smem<N>() + (size_t)N * (sizeof(float2) + 2 * sizeof(float));
+}
+
+// Backward Chebyshev pass before the inverse FFT, in one sweep over a column tile
+// (tile[e * 16 + t]): for each pair of rows (k, N - k), k = 1 .. N/2, a thread forms both Shen
+// stencil outputs (Eq. fast_shen) from the coefficient rows and writes their DCT-III pre-twiddled
+// values; every read precedes the one synchronisation before the writes.  Row 0 keeps its
+// coefficient (no stencil term, no twiddle).  Rows past the basis hold zero.
+template <int N>
+__device__ __forceinline__ void cheb_backward_prepare_tile(float2* buf, int basis, const ChebTables<float>& tb) {
+  using C = float2;
+  constexpr int HALF = N / 2;
+  static_assert((HALF * kTW) % kFastThreads == 0, "whole pairs per thread");
+  constexpr int PH = HALF * kTW / kFastThreads;
+  auto at = [](int t, int e) { return e * kTW + t; };
+  auto stencil = [&](int t, int k) -> C {
+    C v = buf[at(t, k)];
+    if (basis == kDirichlet) {
+      if (k >= 2) v = csub(v, buf[at(t, k - 2)]);
+    } else if (basis == kNeumann) {
+      if (k >= 2) {
+        const float q = tb.c1[k - 2];
+        const C u = buf[at(t, k - 2)];
+        v.x -= q * u.x;
+        v.y -= q * u.y;
+      }
+    } else if (basis == kBiharmonic) {
+      if (k >= 2) {
+        const float be = tb.c1[k - 2];
+        const C u = buf[at(t, k - 2)];
+        v.x += be * u.x;
+        v.y += be * u.y;
+      }
+      if (k >= 4) {
+        const float ga = tb.c2[k - 4];
+        const C u = buf[at(t, k - 4)];
+        v.x += ga * u.x;
+        v.y += ga * u.y;
+      }
+    }
+    return v;
+  };
+  C o1[PH], o2[PH];
+#pragma unroll
+  for (int q = 0; q < PH; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = idx % kTW, k = 1 + idx / kTW;
+    const C x = stencil(t, k);
+    const C y = k < HALF ? stencil(t, N - k) : x;
+    o1[q] = cscale(cmulc(mk<C>(x.x + y.y, x.y - y.x), tb.dctw[k]), 0.5f);
+    o2[q] = cscale(cmulc(mk<C>(y.x + x.y, y.y - x.x), tb.dctw[N - k]), 0.5f);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < PH; ++q) {
+    const int idx = threadIdx.x + q * kFastThreads;
+    const int t = idx % kTW, k = 1 + idx / kTW;
+    buf[at(t, k)] = o1[q];
+    if (k < HALF) buf[at(t, N - k)] = o2[q];
+  }
+  __syncthreads();
+}
 
 // ---- Chebyshev axis, column tiles of [N][inner] ------------------------------------------------
 // MODE kChebScalar: tiles of the complex64 Fourier intermediate -> complex64 spectral array (scalar
@@ -84,10 +149,15 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_cheb_stream(const __grid_co
   extern __shared__ __align__(128) unsigned char smem_raw[];
   C* tiles = reinterpret_cast<C*>(smem_raw);
   Ring ring{reinterpret_cast<uint64_t*>(smem_raw + (size_t)kStages * TILE_BYTES)};
+  C* tw_s = reinterpret_cast<C*>(smem_raw + (size_t)kStages * TILE_BYTES + kStages * sizeof(uint64_t));
+  float* c1_s = reinterpret_cast<float*>(tw_s + N);
+  float* c2_s = c1_s + N;
   const long ntiles = (inner + kTW - 1) / kTW;
   const int nb = basis_count(basis, N);
   if (threadIdx.x == 0) tma::prefetch_map(&map);
-  ring.init();
+  fill_cheb_tables<float>(tw_s, c1_s, c2_s, N, basis, dctw);
+  const ChebTables<float> tabs{tw_s, c1_s, c2_s};
+  ring.init();   // its synchronisation also publishes the tables
   auto issue = [&](long tile, int q) {
     tc::mbar_arrive_expect_tx(&ring.bar[q], TILE_BYTES);
     tma::load_2d(tiles + (size_t)q * N * kTW, &map, (int)(tile * kTW * 2), 0, &ring.bar[q]);
@@ -106,11 +176,11 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_cheb_stream(const __grid_co
       // v_e = x_{2e} (e < N/2), x_{2(N-1-e)+1} (e >= N/2): the even/odd reordering, read by the
       // first FFT pass in place
       fft_cols<N, kTW, kFastThreads, false>(buf, twf, [](int e) { return e < N / 2 ? 2 * e : 2 * (N - 1 - e) + 1; });
-      cheb_forward_finish<float, kChebScalar, float, N, true>(buf, nt, t0, inner, basis, 0, out, dctw);
+      cheb_forward_finish<float, kChebScalar, float, N, true>(buf, nt, t0, inner, basis, 0, out, dctw, &tabs);
     } else {
       for (int idx = threadIdx.x + nb * kTW; idx < N * kTW; idx += kFastThreads) buf[idx] = make_float2(0.f, 0.f);
       __syncthreads();
-      cheb_backward_prepare<float, N, true>(buf, nt, basis, dctw);
+      cheb_backward_prepare_tile<N>(buf, basis, tabs);
       fft_cols<N, kTW, kFastThreads, true>(buf, twf, [](int e) { return e; });
       for (int idx = threadIdx.x; idx < N * kTW; idx += kFastThreads) {
         const int j = idx / kTW, t = idx % kTW;
@@ -301,7 +371,7 @@ cudaError_t persistent_launch_params(K kernel, size_t smem, long ntiles, unsigne
 template <int MODE, int N>
 cudaError_t launch_cheb_n(const CUtensorMap& map, void* out, long inner, int basis, const float2* twf,
                           const float2* dctw, cudaStream_t s) {
-  const size_t smem = cols_smem<N>();
+  const size_t smem = cheb_smem<N>();
   unsigned grid = 1;
   cudaError_t e = persistent_launch_params(k_cheb_stream<MODE, N>, smem, (inner + kTW - 1) / kTW, &grid);
   if (e != cudaSuccess) return e;
