@@ -137,7 +137,10 @@ const char* sgm_status_string(int status);
  *                               stream, device-synchronising) and keep the faster; N > 128
  *                               keeps the FFT method.
  *              The flags are an SGM_ERR_ARG for SGM_F64 spaces.
- * Allocates device tables and workspace on the current device (freed by destroy).
+ * Allocates device tables and workspace on the current device (freed by destroy).  A 3-D space
+ * whose axis 0 is SGM_SHEN_DIRICHLET or SGM_SHEN_BIHARMONIC also holds two factorisation slots
+ * (see the solves below): 2 x (n[0]/2 + 1) x 4 (Dirichlet) or 7 (biharmonic) doubles per Fourier
+ * column and parity, e.g. 2 x 474 MB for the biharmonic basis on a 256^3 box.
  */
 int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n,
                      const double* domain, int precision);
@@ -197,6 +200,21 @@ int sgm_backward(sgm_space* space, const void* u_hat, void* u, void* stream);
  * Works in place (f_tilde == u_hat).  Requires axis 0 = SGM_SHEN_DIRICHLET or
  * SGM_LEGENDRE_DIRICHLET (whose A is diagonal, -(4k+6), and B tridiagonal within a parity).
  * a = b = 0, or a system with a zero pivot, gives SGM_ERR_ARG / non-finite output.
+ */
+/*
+ * Factorisation slots (3-D spaces with a Shen Dirichlet or biharmonic axis 0; the paper builds its
+ * Helmholtz and Biharmonic solvers once from their matrices and applies them to many right-hand
+ * sides, Sec. 4).  The FP64 factorisation of every column system depends only on the operator
+ * (a, b, c) and kappa^2.  Such a space keeps the factorisations of the last two operators it
+ * solved with (the mass solve of sgm_forward counts as one), per column layout (spectral arrays,
+ * or the padded intermediates of the physical-to-physical solves).  A solve with an operator in a
+ * slot replays only the right-hand-side recurrences; a solve with another operator first computes
+ * its factorisation into the least recently used slot, on the call's stream (the first solve with
+ * new coefficients costs about two solves).  Inside a stream capture the solves neither read nor
+ * fill the slots: the captured graph runs kernels that factor as they solve, so it stays valid
+ * whatever later calls store in the slots.  Results are those of the same FP64 arithmetic either
+ * way, up to the order of the back substitution's sums.  Calls on one space must not overlap on the
+ * GPU (they share its workspaces and slots) and must come from one host thread at a time.
  */
 int sgm_helmholtz_solve(sgm_space* space, double a, double b, const void* f_tilde,
                         void* u_hat, void* stream);
