@@ -521,17 +521,19 @@ def run_ours(args):
     hu_p = torch.empty_like(hf_p).pin_memory()
     hu_b = torch.empty_like(hf_b).pin_memory()
 
-    # Steps are pipelined over three streams with double-buffered device arrays: while step i
-    # computes, the inputs of step i+1 are uploaded and the outputs of step i-1 downloaded (all
-    # through pinned host buffers).  Every copy of every timed step lies inside the timed region:
-    # the copy streams start after its first event and the last event waits for them.
+    # Steps are pipelined over four streams with double-buffered device arrays: uploads on one copy
+    # stream, the Poisson solves on the launching stream, the biharmonic solves on the second
+    # stream, downloads on another copy stream (all through pinned host buffers), so that while step
+    # i computes, the inputs of step i+1 are uploaded and the outputs of step i-1 downloaded.  Every
+    # copy of every timed step lies inside the timed region: the other streams start after its first
+    # event and the last event waits for them.
     s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
     fP2, fB2 = [f_p, torch.empty_like(f_p)], [f_b, torch.empty_like(f_b)]
     uP2, uB2 = [u_p, torch.empty_like(u_p)], [u_b, torch.empty_like(u_b)]
 
     def ev():
         return [torch.cuda.Event() for _ in range(2)]
-    in_p, in_b, done_p, done_b, consumed, drained = ev(), ev(), ev(), ev(), ev(), ev()
+    in_p, in_b, done_p, done_b, drained_p, drained_b = ev(), ev(), ev(), ev(), ev(), ev()
     started = [False, False]
 
     def e2e_step(i):
@@ -539,25 +541,31 @@ def run_ours(args):
         main = torch.cuda.current_stream()
         with torch.cuda.stream(s_in):
             if started[j]:
-                s_in.wait_event(consumed[j])           # step i-2 has read buffer j
+                s_in.wait_event(done_p[j])             # step i-2's Poisson solve has read buffer j
             fP2[j].copy_(hf_p, non_blocking=True)
             in_p[j].record(s_in)
+            if started[j]:
+                s_in.wait_event(done_b[j])
             fB2[j].copy_(hf_b, non_blocking=True)
             in_b[j].record(s_in)
         if started[j]:
-            main.wait_event(drained[j])                # step i-2's results have left buffer j
+            main.wait_event(drained_p[j])              # step i-2's result has left buffer j
         main.wait_event(in_p[j])
-        main.wait_event(in_b[j])
-        solve_pair(fP2[j], uP2[j], fB2[j], uB2[j])
+        sp_p.helmholtz(-1.0, 0.0, fP2[j], out=uP2[j])
         done_p[j].record(main)
-        done_b[j].record(main)
-        consumed[j].record(main)
+        with torch.cuda.stream(side):
+            if started[j]:
+                side.wait_event(drained_b[j])
+            side.wait_event(in_b[j])
+            sp_b.biharmonic(1.0, 0.0, 0.0, fB2[j], out=uB2[j])
+            done_b[j].record(side)
         with torch.cuda.stream(s_out):
             s_out.wait_event(done_p[j])
             hu_p.copy_(uP2[j], non_blocking=True)
+            drained_p[j].record(s_out)
             s_out.wait_event(done_b[j])
             hu_b.copy_(uB2[j], non_blocking=True)
-            drained[j].record(s_out)
+            drained_b[j].record(s_out)
         started[j] = True
 
     e2e_steps = max(4, min(args.steps, 10))
@@ -569,10 +577,12 @@ def run_ours(args):
     a.record(stream)
     s_in.wait_event(a)
     s_out.wait_event(a)
+    side.wait_event(a)
     for i in range(e2e_steps):
         e2e_step(i)
     stream.wait_stream(s_in)
     stream.wait_stream(s_out)
+    stream.wait_stream(side)
     b.record(stream)
     b.synchronize()
     e2e_ms = max_over_ranks(a.elapsed_time(b) / e2e_steps, "cuda")
@@ -601,6 +611,10 @@ def run_ours(args):
             "data": "synthetic (manufactured u=(1-x^2)^2 sin y cos 2z)",
             "config": config_of(world),
             "error_vs_exact": {"poisson": err_p, "biharmonic": err_b},
+            "eliminations": ("FP64, factored once per space and operator (in the warm-up steps) and replayed in "
+                             "the timed steps; a biharmonic solve with a new operator (factorisation + solve, FP64 "
+                             f"data): {br['biharmonic_factorise_and_solve_ms']:.3f} ms against "
+                             f"{br['biharmonic_solve_kernel_ms']:.3f} ms replayed"),
             "breakdown_ms": {k: round(v, 4) for k, v in br.items()},
             "roofline": roofline,
             "hbm_strict": strict,
