@@ -175,42 +175,77 @@ __global__ void __launch_bounds__(128) k_batch_solve2(const BatchProblem* __rest
     x[3] = Bn;
   }
   __syncthreads();
+  // side 0 forms u_{h-1}; after one synchronisation side 0 back-substitutes rows h-2 .. 0 while
+  // side 1 forward-substitutes rows h .. n-1, each through a ring of scratch loads issued ahead
+  double un = 0.0, Ts = 0.0;
   if (side == 0 && h > 0) {
     const double ah = x[0], Ah = x[1], bh = x[2], Bh = x[3];
     const double u = fma(-gl, Ah, fma(-ell, ah, fl)) * rcp64b(fma(gl, Bh, fma(ell, bh, dl)));
     x[4] = u;
     U[rbase + (long)(p + 2 * (h - 1)) * 32] = u;
-    double un = u, Ts = fma(Bh, u, Ah);   // T_h
-    double* s = h > 1 ? s0 + (long)(h - 2) * 96 : s0;
-    double rn = 0.0, gn = 0.0, fb = 0.0;
-    if (h > 1) {
-      rn = s[0];
-      gn = s[32];
-      fb = s[64];
-    }
-    for (int i = h - 2; i >= 0; --i) {
-      const int k = p + 2 * i;
-      const double r = rn, g = gn, f = fb;
-      if (i > 0) {
-        s -= 96;
-        rn = s[0];
-        gn = s[32];
-        fb = s[64];
-      }
-      Ts += un;
-      const double uu = fma(-g, Ts, fma(-ell, un, f)) * r;
-      U[rbase + (long)k * 32] = uu;
-      un = uu;
-    }
+    un = u;
+    Ts = fma(Bh, u, Ah);   // T_h
   }
   __syncthreads();
-  if (side == 1 && n > h) {
+  if (side == 0) {
+    // ring slot d of pass j0 holds (r, g, f) of row h - 2 - (j0 + d)
+    constexpr int D0 = 4;
+    double rb[D0], gb[D0], fb[D0];
+#pragma unroll
+    for (int d = 0; d < D0; ++d)
+      if (h - 2 - d >= 0) {
+        const double* s = s0 + (long)(h - 2 - d) * 96;
+        rb[d] = s[0];
+        gb[d] = s[32];
+        fb[d] = s[64];
+      }
+    for (int j0 = 0; j0 < h - 1; j0 += D0) {
+#pragma unroll
+      for (int d = 0; d < D0; ++d) {
+        const int i = h - 2 - (j0 + d);
+        if (i >= 0) {
+          const double r = rb[d], g = gb[d], f = fb[d];
+          if (i - D0 >= 0) {
+            const double* s = s0 + (long)(i - D0) * 96;
+            rb[d] = s[0];
+            gb[d] = s[32];
+            fb[d] = s[64];
+          }
+          Ts += un;
+          const double uu = fma(-g, Ts, fma(-ell, un, f)) * r;
+          U[rbase + (long)(p + 2 * i) * 32] = uu;
+          un = uu;
+        }
+      }
+    }
+  } else if (n > h) {
+    // ring slot d of pass i0 holds (b_i, a_i) of row i0 + d
+    constexpr int D1 = 8;
     double up = h > 0 ? x[4] : 0.0;
-    for (int i = h; i < n; ++i) {
-      const double* s = s0 + (long)i * 96;
-      const double uu = fma(s[0], up, s[32]);
-      U[rbase + (long)(p + 2 * i) * 32] = uu;
-      up = uu;
+    double bb[D1], ab[D1];
+#pragma unroll
+    for (int d = 0; d < D1; ++d)
+      if (h + d < n) {
+        const double* s = s0 + (long)(h + d) * 96;
+        bb[d] = s[0];
+        ab[d] = s[32];
+      }
+    for (int i0 = h; i0 < n; i0 += D1) {
+#pragma unroll
+      for (int d = 0; d < D1; ++d) {
+        const int i = i0 + d;
+        if (i < n) {
+          const double bi = bb[d], ai = ab[d];
+          if (i + D1 < n) {
+            const double* s = s0 + (long)(i + D1) * 96;
+            bb[d] = s[0];
+            ab[d] = s[32];
+          }
+          const double uu = fma(bi, up, ai);
+          U[rbase + (long)(p + 2 * i) * 32] = uu;
+          up = uu;
+        }
+      }
     }
   }
 }

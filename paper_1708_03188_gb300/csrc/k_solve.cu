@@ -534,51 +534,64 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
       x[4 * NC + 1] = Bn;
     }
     __syncthreads();
+    // side 0 forms u_{h-1} from the reduced top row and side 1's (a_h, b_h, A_h, B_h); after one
+    // synchronisation side 0 back-substitutes rows h-2 .. 0 while side 1 forward-substitutes rows
+    // h .. n-1, each sweep reading its rows from the scratch through a ring of loads issued ahead
+    double2 un[NC], Ts[NC];
+    if (side == 0 && h > 0) {
+      const double bh = x[4 * NC], Bh = x[4 * NC + 1];
+      const double rd = rcp64(fma(gl, Bh, fma(ell, bh, dl)));
+#pragma unroll
+      for (int q = 0; q < NC; ++q) {
+        const double2 ah = make_double2(x[4 * q], x[4 * q + 1]), Ah = make_double2(x[4 * q + 2], x[4 * q + 3]);
+        double2 u;
+        u.x = fma(-gl, Ah.x, fma(-ell, ah.x, fl[q].x)) * rd;
+        u.y = fma(-gl, Ah.y, fma(-ell, ah.y, fl[q].y)) * rd;
+        x[4 * NC + 2 + 2 * q] = u.x;           // u_{h-1} for side 1
+        x[4 * NC + 3 + 2 * q] = u.y;
+        // u_h = a_h + b_h u_{h-1},  T_h = A_h + B_h u_{h-1}
+        un[q] = u;
+        Ts[q] = make_double2(fma(Bh, u.x, Ah.x), fma(Bh, u.y, Ah.y));
+        if (valid) st2<TO>(out, off[q] + (long)(h - 1) * rstep, real, u);
+      }
+    }
+    __syncthreads();
     if (side == 0) {
-      double2 un[NC], Ts[NC];
-      if (h > 0) {
-        const double bh = x[4 * NC], Bh = x[4 * NC + 1];
-        const double rd = rcp64(fma(gl, Bh, fma(ell, bh, dl)));
+      // back substitution of rows h-2 .. 0 (Ts = T_{i+1} after adding u_{i+1}); side 0 wrote row i
+      // at scratch slot i; ring slot d of pass j0 holds row h - 2 - (j0 + d)
+      constexpr int D0 = 2;
+      const double* base0 = scratch + gt;
+      double vb[D0][NV];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          const double2 ah = make_double2(x[4 * q], x[4 * q + 1]), Ah = make_double2(x[4 * q + 2], x[4 * q + 3]);
-          double2 u;
-          u.x = fma(-gl, Ah.x, fma(-ell, ah.x, fl[q].x)) * rd;
-          u.y = fma(-gl, Ah.y, fma(-ell, ah.y, fl[q].y)) * rd;
-          x[4 * NC + 2 + 2 * q] = u.x;           // u_{h-1} for side 1
-          x[4 * NC + 3 + 2 * q] = u.y;
-          // u_h = a_h + b_h u_{h-1},  T_h = A_h + B_h u_{h-1}
-          un[q] = u;
-          Ts[q] = make_double2(fma(Bh, u.x, Ah.x), fma(Bh, u.y, Ah.y));
-          if (valid) st2<TO>(out, off[q] + (long)(h - 1) * rstep, real, u);
+      for (int d = 0; d < D0; ++d)
+        if (h - 2 - d >= 0) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) vb[d][v] = base0[(long)(h - 2 - d) * sstep + v * nth];
         }
-      }
-      // back substitution of rows h-2 .. 0 (Ts = T_{i+1} after adding u_{i+1})
-      double vn[NV];
-      if (h > 1) {
-        s -= 2 * sstep;   // row h-2 (s was one past row h-1)
+      for (int j0 = 0; j0 < h - 1; j0 += D0) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) vn[v] = s[v * nth];
-      }
-      for (int i = h - 2; i >= 0; --i) {
-        double v[NV];
+        for (int d = 0; d < D0; ++d) {
+          const int i = h - 2 - (j0 + d);
+          if (i >= 0) {
+            double v[NV];
 #pragma unroll
-        for (int j = 0; j < NV; ++j) v[j] = vn[j];
-        if (i > 0) {
-          s -= sstep;
+            for (int t = 0; t < NV; ++t) v[t] = vb[d][t];
+            if (i - D0 >= 0) {
 #pragma unroll
-          for (int j = 0; j < NV; ++j) vn[j] = s[j * nth];
-        }
-        const double r = v[0], g = v[1];
+              for (int t = 0; t < NV; ++t) vb[d][t] = base0[(long)(i - D0) * sstep + t * nth];
+            }
+            const double r = v[0], g = v[1];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          Ts[q].x += un[q].x;
-          Ts[q].y += un[q].y;
-          double2 u;
-          u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
-          u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
-          if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
-          un[q] = u;
+            for (int q = 0; q < NC; ++q) {
+              Ts[q].x += un[q].x;
+              Ts[q].y += un[q].y;
+              double2 u;
+              u.x = fma(-g, Ts[q].x, fma(-ell, un[q].x, v[2 + 2 * q])) * r;
+              u.y = fma(-g, Ts[q].y, fma(-ell, un[q].y, v[3 + 2 * q])) * r;
+              if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
+              un[q] = u;
+            }
+          }
         }
       }
       if (valid)
@@ -586,26 +599,43 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
 #pragma unroll
           for (int q = 0; q < NC; ++q) st2<TO>(out, (long)k * ncols + cc[q], real, make_double2(0.0, 0.0));
         }
-    }
-    __syncthreads();
-    if (side == 1) {
-      // forward substitution of rows h .. n-1 from u_{h-1}
+    } else {
+      // forward substitution of rows h .. n-1 from u_{h-1}; side 1 wrote rows n-1 .. h at scratch
+      // slots 0 .. n-1-h (row i is slot n-1-i); ring slot d of pass i0 holds row i0 + d
+      constexpr int D1 = 4;
       double2 up[NC];
 #pragma unroll
       for (int q = 0; q < NC; ++q)
         up[q] = h > 0 ? make_double2(x[4 * NC + 2 + 2 * q], x[4 * NC + 3 + 2 * q]) : make_double2(0.0, 0.0);
-      // side 1 wrote rows n-1 .. h at scratch slots 0 .. n-1-h; row i is slot n-1-i
-      double* base = scratch + gt;
-      for (int i = h; i < n; ++i) {
-        const double* sr = base + (long)(n - 1 - i) * sstep;
-        const double bi = sr[0];
+      const double* base = scratch + gt;
+      double rb[D1][1 + 2 * NC];
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          double2 u;
-          u.x = fma(bi, up[q].x, sr[(1 + 2 * q) * nth]);
-          u.y = fma(bi, up[q].y, sr[(2 + 2 * q) * nth]);
-          if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
-          up[q] = u;
+      for (int d = 0; d < D1; ++d)
+        if (h + d < n) {
+#pragma unroll
+          for (int v = 0; v < 1 + 2 * NC; ++v) rb[d][v] = base[(long)(n - 1 - (h + d)) * sstep + v * nth];
+        }
+      for (int i0 = h; i0 < n; i0 += D1) {
+#pragma unroll
+        for (int d = 0; d < D1; ++d) {
+          const int i = i0 + d;
+          if (i < n) {
+            double a[1 + 2 * NC];
+#pragma unroll
+            for (int t = 0; t < 1 + 2 * NC; ++t) a[t] = rb[d][t];
+            if (i + D1 < n) {
+#pragma unroll
+              for (int t = 0; t < 1 + 2 * NC; ++t) rb[d][t] = base[(long)(n - 1 - (i + D1)) * sstep + t * nth];
+            }
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              double2 u;
+              u.x = fma(a[0], up[q].x, a[1 + 2 * q]);
+              u.y = fma(a[0], up[q].y, a[2 + 2 * q]);
+              if (valid) st2<TO>(out, off[q] + (long)i * rstep, real, u);
+              up[q] = u;
+            }
+          }
         }
       }
     }
@@ -1295,18 +1325,23 @@ static cudaError_t solve_nc(int basis, bool real, double a, double b, double c, 
     // Four warps per 32 work items, each thread at most ceil(n / 2) rows of
     // scratch; the grid is sized so that the scratch allocated for the one-sided kernel (N/2 + 1
     // rows per thread of scratch_threads) holds every thread's rows
-    const long nwb = (cm.nitems + 31) / 32;
-    const long rows_full = N / 2 + 1, n0 = (N - 2 + 1) / 2, rows_split = (n0 + 1) / 2 + 1;
-    long cap = scratch_threads * rows_full / rows_split;
-    cap = std::max(128L, (cap / 128) * 128);
-    const long thr = std::min(cap, nwb * 128);
-    const unsigned grid2 = (unsigned)std::max(1L, thr / 128);
-    const size_t smem = sizeof(double) * (2 * ts + 2 * 32 * (6 * NC + 2));
-    if (smem > 48 * 1024 &&
-        (e = cudaFuncSetAttribute(k_solve_dirichlet2<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
-      return e;
-    k_solve_dirichlet2<T, NC, TO><<<grid2, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts, scratch);
+    if constexpr (NC != 1) {
+      return cudaErrorInvalidValue;
+    } else {
+      const long nwb = (cm.nitems + 31) / 32;
+      const long rows_full = N / 2 + 1, n0 = (N - 2 + 1) / 2, rows_split = (n0 + 1) / 2 + 1;
+      long cap = scratch_threads * rows_full / rows_split;
+      cap = std::max(128L, (cap / 128) * 128);
+      const long thr = std::min(cap, nwb * 128);
+      const unsigned grid2 = (unsigned)std::max(1L, thr / 128);
+      const size_t smem = sizeof(double) * (2 * ts + 2 * 32 * (6 * NC + 2));
+      if (smem > 48 * 1024 &&
+          (e = cudaFuncSetAttribute(k_solve_dirichlet2<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem)) != cudaSuccess)
+        return e;
+      k_solve_dirichlet2<T, NC, TO><<<grid2, 128, smem, s>>>(in, out, N, ncols, real ? 1 : 0, a, b, wn, cm, tab, ts,
+                                                             scratch);
+    }
   } else if (basis == kDirichlet) {
     const size_t smem = sizeof(double) * 2 * ts;
     if (smem > 48 * 1024 && (e = cudaFuncSetAttribute(k_solve_dirichlet<T, NC, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
