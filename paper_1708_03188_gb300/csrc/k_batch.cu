@@ -110,64 +110,77 @@ __global__ void __launch_bounds__(128) k_batch_solve2(const BatchProblem* __rest
   double* s0 = scratch + sbase[wslot] * 2 + (long)p * (sbase[wslot + 1] - sbase[wslot]) + lane;   // slot of row 0
   double* x = xch[p][lane];
   double dl = 1.0, gl = 0.0, fl = 0.0;
+  // the operands of a row (right-hand side, stiffness and mass coefficients) come through a ring
+  // of DM rows of loads issued ahead: a row's FP64 work is shorter than the load latency
+  constexpr int DM = 4;
+  double fb[DM], mb[DM];
+  double2 cb[DM];
+  auto load_row = [&](int d, int i) {
+    const int k = p + 2 * i;
+    fb[d] = S[rbase + (long)k * 32];
+    cb[d] = __ldg(&coef[k]);
+    mb[d] = __ldg(&mass[k]);
+  };
   if (side == 0) {
     double pr_ = 0.0, pg = 0.0, pge = 0.0, pf = 0.0;
-    double fn = h > 0 ? S[rbase + (long)p * 32] : 0.0;
-    double2 cn = h > 0 ? __ldg(&coef[p]) : make_double2(0.0, 0.0);
-    double mn = h > 0 ? __ldg(&mass[p]) : 0.0;
-    double* s = s0;
-    for (int i = 0; i < h; ++i) {
-      const int k = p + 2 * i;
-      double f = fn;
-      const double2 c = cn;
-      const double mk2 = mn;
-      if (i + 1 < h) {
-        fn = S[rbase + (long)(k + 2) * 32];
-        cn = __ldg(&coef[k + 2]);
-        mn = __ldg(&mass[k + 2]);
+#pragma unroll
+    for (int d = 0; d < DM; ++d)
+      if (d < h) load_row(d, d);
+    for (int i0 = 0; i0 < h; i0 += DM) {
+#pragma unroll
+      for (int d = 0; d < DM; ++d) {
+        const int i = i0 + d;
+        if (i < h) {
+          double f = fb[d];
+          const double2 c = cb[d];
+          const double mk2 = mb[d];
+          if (i + DM < h) load_row(d, i + DM);
+          double dd = fma(aB, mk2, c.x);
+          double g = c.y;
+          if (i > 0) {
+            const double mu = ell * pr_;
+            dd = fma(-mu, pge, dd);
+            g = fma(-mu, pg, g);
+            f = fma(-mu, pf, f);
+          }
+          const double r = rcp64b(dd);
+          double* s = s0 + (long)i * 96;
+          s[0] = r;
+          s[32] = g;
+          s[64] = f;
+          pr_ = r; pg = g; pge = g + ell; pf = f;
+          dl = dd; gl = g; fl = f;
+        }
       }
-      double d = fma(aB, mk2, c.x);
-      double g = c.y;
-      if (i > 0) {
-        const double mu = ell * pr_;
-        d = fma(-mu, pge, d);
-        g = fma(-mu, pg, g);
-        f = fma(-mu, pf, f);
-      }
-      const double r = rcp64b(d);
-      s[0] = r;
-      s[32] = g;
-      s[64] = f;
-      s += 96;
-      pr_ = r; pg = g; pge = g + ell; pf = f;
-      dl = d; gl = g; fl = f;
     }
   } else {
     double bn = 0.0, Bn = 0.0, an = 0.0, An = 0.0;
-    double fn = n > h ? S[rbase + (long)(p + 2 * (n - 1)) * 32] : 0.0;
-    double2 cn = n > h ? __ldg(&coef[p + 2 * (n - 1)]) : make_double2(0.0, 0.0);
-    double mn = n > h ? __ldg(&mass[p + 2 * (n - 1)]) : 0.0;
-    for (int i = n - 1; i >= h; --i) {
-      const int k = p + 2 * i;
-      const double f = fn;
-      const double2 c = cn;
-      const double mk2 = mn;
-      if (i - 1 >= h) {
-        fn = S[rbase + (long)(k - 2) * 32];
-        cn = __ldg(&coef[k - 2]);
-        mn = __ldg(&mass[k - 2]);
+    // ring slot d of pass j0 holds row n - 1 - (j0 + d)
+#pragma unroll
+    for (int d = 0; d < DM; ++d)
+      if (n - 1 - d >= h) load_row(d, n - 1 - d);
+    for (int j0 = 0; j0 < n - h; j0 += DM) {
+#pragma unroll
+      for (int d = 0; d < DM; ++d) {
+        const int i = n - 1 - (j0 + d);
+        if (i >= h) {
+          const double f = fb[d];
+          const double2 c = cb[d];
+          const double mk2 = mb[d];
+          if (i - DM >= h) load_row(d, i - DM);
+          const double dd = fma(aB, mk2, c.x), g = c.y;
+          const double R = rcp64b(fma(g, Bn, fma(ell, bn, dd)));
+          const double bi = -ell * R, onep = 1.0 + Bn;
+          const double ai = fma(-g, An, fma(-ell, an, f)) * R;
+          double* s = s0 + (long)i * 96;
+          s[0] = bi;
+          s[32] = ai;
+          An = fma(onep, ai, An);
+          Bn = onep * bi;
+          an = ai;
+          bn = bi;
+        }
       }
-      const double d = fma(aB, mk2, c.x), g = c.y;
-      const double R = rcp64b(fma(g, Bn, fma(ell, bn, d)));
-      const double bi = -ell * R, onep = 1.0 + Bn;
-      const double ai = fma(-g, An, fma(-ell, an, f)) * R;
-      double* s = s0 + (long)i * 96;
-      s[0] = bi;
-      s[32] = ai;
-      An = fma(onep, ai, An);
-      Bn = onep * bi;
-      an = ai;
-      bn = bi;
     }
     x[0] = an;
     x[1] = An;

@@ -441,23 +441,34 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
     double2 fl[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) fl[q] = make_double2(0.0, 0.0);
+    // right-hand sides come through a ring of DM rows of loads issued ahead (kept as loaded,
+    // widened when used): a row's FP64 work is shorter than the load latency
+    constexpr int DM = 4;
+    cplx<T> fr[DM][NC];
     if (side == 0) {
       double pr = 0.0, pge = 0.0, pg = 0.0;
       double2 pf[NC];
-      cplx<T> fn[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        pf[q] = make_double2(0.0, 0.0);
-        if (valid && h > 0) fn[q] = ldraw<T>(in, off[q], real);
-      }
+      for (int q = 0; q < NC; ++q) pf[q] = make_double2(0.0, 0.0);
+#pragma unroll
+      for (int d = 0; d < DM; ++d)
+        if (valid && d < h) {
+#pragma unroll
+          for (int q = 0; q < NC; ++q) fr[d][q] = ldraw<T>(in, off[q] + (long)d * rstep, real);
+        }
       for (int i = 0; i < h; ++i) {
         const int k = p + 2 * i;
         double2 f[NC];
+        const int slot = i % DM;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          f[q] = (valid && h > 0) ? widen2<T>(fn[q]) : make_double2(0.0, 0.0);
-          if (valid && i + 1 < h) fn[q] = ldraw<T>(in, off[q] + (long)(i + 1) * rstep, real);
-        }
+        for (int dd = 0; dd < DM; ++dd)
+          if (dd == slot) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              f[q] = valid ? widen2<T>(fr[dd][q]) : make_double2(0.0, 0.0);
+              if (valid && i + DM < h) fr[dd][q] = ldraw<T>(in, off[q] + (long)(i + DM) * rstep, real);
+            }
+          }
         double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
         double g = aG[k];
         if (i > 0) {
@@ -488,20 +499,28 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet2(const void* __restrict
     } else {
       double bn = 0.0, Bn = 0.0;
       double2 an[NC], An[NC];
-      cplx<T> fn[NC];
 #pragma unroll
-      for (int q = 0; q < NC; ++q) {
-        an[q] = An[q] = make_double2(0.0, 0.0);
-        if (valid && n > h) fn[q] = ldraw<T>(in, off[q] + (long)(n - 1) * rstep, real);
-      }
+      for (int q = 0; q < NC; ++q) an[q] = An[q] = make_double2(0.0, 0.0);
+      // ring slot (n - 1 - i) % DM holds row i
+#pragma unroll
+      for (int d = 0; d < DM; ++d)
+        if (valid && n - 1 - d >= h) {
+#pragma unroll
+          for (int q = 0; q < NC; ++q) fr[d][q] = ldraw<T>(in, off[q] + (long)(n - 1 - d) * rstep, real);
+        }
       for (int i = n - 1; i >= h; --i) {
         const int k = p + 2 * i;
         double2 f[NC];
+        const int slot = (n - 1 - i) % DM;
 #pragma unroll
-        for (int q = 0; q < NC; ++q) {
-          f[q] = valid ? widen2<T>(fn[q]) : make_double2(0.0, 0.0);
-          if (valid && i - 1 >= h) fn[q] = ldraw<T>(in, off[q] + (long)(i - 1) * rstep, real);
-        }
+        for (int dd = 0; dd < DM; ++dd)
+          if (dd == slot) {
+#pragma unroll
+            for (int q = 0; q < NC; ++q) {
+              f[q] = valid ? widen2<T>(fr[dd][q]) : make_double2(0.0, 0.0);
+              if (valid && i - DM >= h) fr[dd][q] = ldraw<T>(in, off[q] + (long)(i - DM) * rstep, real);
+            }
+          }
         const double d = aA0[k] + (k == 0 ? aB * 4.71238898038469 : aBpi);
         const double g = aG[k];
         const double R = rcp64(fma(g, Bn, fma(ell, bn, d)));
