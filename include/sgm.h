@@ -139,8 +139,8 @@ const char* sgm_status_string(int status);
  *              The flags are an SGM_ERR_ARG for SGM_F64 spaces.
  * Allocates device tables and workspace on the current device (freed by destroy).  A 3-D space
  * whose axis 0 is SGM_SHEN_DIRICHLET or SGM_SHEN_BIHARMONIC also holds two factorisation slots
- * (see the solves below): 2 x (n[0]/2 + 1) x 4 (Dirichlet) or 7 (biharmonic) doubles per Fourier
- * column and parity, e.g. 2 x 474 MB for the biharmonic basis on a 256^3 box.
+ * (see the solves below): 2 x (n[0]/2 + 1) x 4 (Dirichlet) or 7 (biharmonic) doubles per pair of
+ * Fourier columns +-l1 and parity, e.g. 2 x 237 MB for the biharmonic basis on a 256^3 box.
  */
 int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t* n,
                      const double* domain, int precision);

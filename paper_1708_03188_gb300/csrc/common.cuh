@@ -141,12 +141,14 @@ cudaError_t launch_solve_f64_to_f32(int basis, double a, double b, double c, con
                                     const int2* groups, long ngroups, cudaStream_t s);
 // Factored eliminations of 3-D spaces (k_solve.cu): FP64 values per row and work thread of a
 // factorisation table (0: the basis has none), work threads of the table for a call's column
-// layout (0: a 1-D or 2-D space, no factored form), the factorisation of the operator (a, b, c)
+// layout (0: a 1-D or 2-D space, no factored form), the work threads of the solve itself (one per
+// column and parity; their scratch rows), the factorisation of the operator (a, b, c)
 // into a table of rows x values x threads doubles, and the solve replaying a table (TI, TO:
 // spectral input and output types; the table must come from launch_factor with the same basis, N,
 // columns and wavenumbers; scratch_threads: threads the scratch holds 2 doubles per row for).
 int solve_factor_values(int basis);
 long solve_factor_threads(long ncols, const Wavenumbers& wn);
+long solve_factored_scratch_threads(long ncols, const Wavenumbers& wn);   // threads of the solve
 cudaError_t launch_factor(int basis, double a, double b, double c, int N, long ncols, const Wavenumbers& wn,
                           const double* tab, double* fact, cudaStream_t s);
 template <typename TI, typename TO>

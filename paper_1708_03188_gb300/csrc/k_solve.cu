@@ -838,10 +838,11 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
 // k_factor_* runs the top-down factorisation of the kernels above and stores it per work item in
 // a table laid out [row][value][work thread] (work thread = 32 * warp + lane of the work
 // decomposition above, so a warp reads 256 contiguous bytes per value); k_solve_*_f replays only
-// the right-hand-side recurrences from the table.  Both run one thread per column and parity
-// (NC = 1): with no factorisation left to share between the columns of a thread, single columns
-// give four times the warps of the four-column groups, to hide the FP64 latency and to share the
-// SMs with a concurrent solve's kernels in small, even units (and a quarter of the registers).
+// the right-hand-side recurrences from the table.  The solves run one thread per column and
+// parity (NC = 1): with no factorisation left to share between the columns of a thread, single
+// columns give four times the warps of the four-column groups, to hide the FP64 latency and to
+// share the SMs with a concurrent solve's kernels in small, even units (and a quarter of the
+// registers).  The table holds one entry per pair of columns +-l1 (k_factor_*<2>), read by both.
 // FP64 operations per row and complex column: Dirichlet 10 (against 16 with the factorisation
 // shared by a pair of columns), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal pivots are the same FP64
 // values the kernels above compute; the back substitution adds the term of the unknown just
@@ -904,6 +905,26 @@ __global__ void __launch_bounds__(128) k_factor_dirichlet(int N, double a, doubl
   }
 }
 
+// Factorisation table of the factored solves: the columns (l1, l2) and (-l1, l2) have the same
+// kappa2, so with kPairTable one table entry per pair +-l1 (written by k_factor_*<2>, the pair
+// decomposition of the kernels above) serves both columns, whose threads read it at about the same
+// time (the partner's read then hits L2); without it every column thread has its own entry
+// (k_factor_*<1>).  table_items: the entries of a parity; table_thread: the entry of a column.
+constexpr bool kPairTable = true;
+
+__device__ __forceinline__ long table_items(const ColumnMap& cm) {
+  if (!kPairTable) return cm.nitems;
+  const int M1 = cm.pair_m1;
+  return (1 + (M1 - 1) / 2 + (M1 % 2 == 0 ? 1 : 0)) * (long)cm.n2;
+}
+__device__ __forceinline__ long table_thread(const ColumnMap& cm, long w, int lane, long item, int p) {
+  if (!kPairTable) return w * 32 + lane;
+  const long i1 = item / cm.n2, i2 = item - i1 * cm.n2;
+  const long g = 2 * i1 <= cm.pair_m1 ? i1 : cm.pair_m1 - i1;
+  const long it = g * cm.n2 + i2;
+  return (2 * (it >> 5) + p) * 32 + (it & 31);
+}
+
 // The factored sweeps do little FP64 work per row (the Dirichlet forward sweep 2 FMAs per
 // column). Each sweep keeps a ring of D rows of operands in registers (the loads of row i + D are
 // issued as row i is consumed; a slot is indexed by a compile-time position of the unrolled ring)
@@ -923,7 +944,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet_f(const void* __restric
   const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const long nwb = (cm.nitems + 31) / 32;
-  const long TT = 2 * nwb * 32;
+  const long TT = 2 * ((table_items(cm) + 31) / 32) * 32;
   const long fs = FD_COUNT * TT;   // table stride of one row
   const int nb = N - 2;
   const cplx<T>* src = reinterpret_cast<const cplx<T>*>(in);
@@ -934,7 +955,7 @@ __global__ void __launch_bounds__(128) k_solve_dirichlet_f(const void* __restric
     long cc[NC];
     map_columns<NC>(cm, item, cc);
     const int n = (nb - p + 1) / 2;
-    const double* fr = fact + w * 32 + lane;
+    const double* fr = fact + table_thread(cm, w, lane, item, p);
     long off[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
@@ -1155,7 +1176,7 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
   const long gt = (long)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const long nwb = (cm.nitems + 31) / 32;
-  const long TT = 2 * nwb * 32;
+  const long TT = 2 * ((table_items(cm) + 31) / 32) * 32;
   const long fs = FB_COUNT * TT;
   const int nb = N - 4;
   const cplx<T>* src = reinterpret_cast<const cplx<T>*>(in);
@@ -1166,7 +1187,7 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic_f(const void* __restri
     long cc[NC];
     map_columns<NC>(cm, item, cc);
     const int n = (nb - p + 1) / 2;
-    const double* fr = fact + w * 32 + lane;
+    const double* fr = fact + table_thread(cm, w, lane, item, p);
     long off[NC];
 #pragma unroll
     for (int q = 0; q < NC; ++q) off[q] = (long)p * ncols + cc[q];
@@ -1415,7 +1436,7 @@ int solve_factor_values(int basis) { return basis == kDirichlet ? FD_COUNT : bas
 // Work decomposition of the factored solves of 3-D spaces: one thread per column and parity.
 static ColumnMap factored_map(long ncols, const Wavenumbers& wn, bool* ok) {
   ColumnMap cm;
-  cm.pair_m1 = 0;
+  cm.pair_m1 = wn.n1;   // read by table_thread only
   cm.n2 = wn.n2;
   cm.nitems = ncols;
   cm.groups = nullptr;
@@ -1424,6 +1445,17 @@ static ColumnMap factored_map(long ncols, const Wavenumbers& wn, bool* ok) {
 }
 
 long solve_factor_threads(long ncols, const Wavenumbers& wn) {
+  bool ok = false;
+  const ColumnMap cm = factored_map(ncols, wn, &ok);
+  if (!ok) return 0;
+  if (kPairTable) {
+    int nc = 0;
+    return 2 * ((column_map(ncols, wn, nullptr, 0, &nc).nitems + 31) / 32) * 32;
+  }
+  return 2 * ((cm.nitems + 31) / 32) * 32;
+}
+
+long solve_factored_scratch_threads(long ncols, const Wavenumbers& wn) {
   bool ok = false;
   const ColumnMap cm = factored_map(ncols, wn, &ok);
   return ok ? 2 * ((cm.nitems + 31) / 32) * 32 : 0;
@@ -1460,6 +1492,11 @@ cudaError_t launch_factor(int basis, double a, double b, double c, int N, long n
   bool ok = false;
   const ColumnMap cm = factored_map(ncols, wn, &ok);
   if (!ok || solve_factor_values(basis) == 0) return cudaErrorInvalidValue;
+  if (kPairTable) {
+    int nc = 0;
+    const ColumnMap cm2 = column_map(ncols, wn, nullptr, 0, &nc);
+    return factor_nc<2>(basis, a, b, c, N, wn, cm2, tab, fact, s);
+  }
   return factor_nc<1>(basis, a, b, c, N, wn, cm, tab, fact, s);
 }
 

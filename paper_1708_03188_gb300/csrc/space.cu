@@ -451,7 +451,7 @@ int eliminate(sgm_space* s, int basis, double a, double b, double c, const void*
     }
     s->fact_use[slot] = ++s->fact_clock;
     return wrap(launch_solve_factored_to<TI, TO>(basis, s->real_spec, in, out, N, ncols, wn, s->tab, s->fact[slot],
-                                                 s->scratch, s->fact_threads, st),
+                                                 s->scratch, s->fact_scratch_threads, st),
                 "solve");
   }
   if constexpr (std::is_same<TI, TO>::value)
@@ -782,12 +782,15 @@ int sgm_space_create(sgm_space** out, int ndim, const int* kinds, const int64_t*
       if (st == SGM_OK && ndim == 3 && nvf > 0) {
         Wavenumbers wn = wavenumbers(s);
         long thr = solve_factor_threads(s->nspec / N, wn);
+        long sthr = solve_factored_scratch_threads(s->nspec / N, wn);
         if (s->stream) {
           wn.n2 = s->hp;
           thr = std::max(thr, solve_factor_threads(s->inner_p, wn));
+          sthr = std::max(sthr, solve_factored_scratch_threads(s->inner_p, wn));
         }
-        s->fact_threads = ((thr + 127) / 128) * 128;
-        scratch_bytes = std::max(scratch_bytes, sizeof(double) * rows * 2 * s->fact_threads);
+        s->fact_threads = thr;
+        s->fact_scratch_threads = ((sthr + 127) / 128) * 128;
+        scratch_bytes = std::max(scratch_bytes, sizeof(double) * rows * 2 * s->fact_scratch_threads);
         for (int i = 0; i < 2 && st == SGM_OK; ++i)
           chk(cudaMalloc(&s->fact[i], sizeof(double) * rows * nvf * s->fact_threads), "factorisation table");
       }

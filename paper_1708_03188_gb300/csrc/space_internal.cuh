@@ -36,16 +36,17 @@ struct sgm_space {
   long ngroups = 0;
   int solve_nc = 1;          // columns per elimination thread (1, 2 or 4)
   // factorisation tables of the 3-D Dirichlet and biharmonic eliminations (k_solve.cu
-  // launch_factor, one thread per column and parity): two slots of rows x values x fact_threads
-  // doubles, each keyed by the operator and column layout it holds (basis, a, b, c, n2) and
-  // replaced least recently used; the scratch holds the factored solves' rows for fact_threads
-  // threads
+  // launch_factor, one entry per pair of columns +-l1 and parity): two slots of rows x values x
+  // fact_threads doubles, each keyed by the operator and column layout it holds (basis, a, b, c,
+  // n2) and replaced least recently used; the scratch holds the factored solves' rows (one thread
+  // per column and parity) for fact_scratch_threads threads
   double* fact[2] = {nullptr, nullptr};
   double fact_key[2][5] = {{0, 0, 0, 0, 0}, {0, 0, 0, 0, 0}};
   bool fact_valid[2] = {false, false};
   unsigned long fact_use[2] = {0, 0};
   unsigned long fact_clock = 0;
-  long fact_threads = 0;
+  long fact_threads = 0;          // table threads of a slot
+  long fact_scratch_threads = 0;  // threads of a factored solve (scratch rows)
   int cheb_tc = 0;           // 1: Chebyshev axis by the tensor-core contraction (k_cheb_tc.cu)
   void* tc_img[3] = {nullptr, nullptr, nullptr};  // contraction matrices per ChebMode
   void* pdx_tab = nullptr;   // Shen-to-Chebyshev stencil coefficients of sgm_project_dx (project.cu)
