@@ -163,7 +163,7 @@ def hbm_peak():
 FLOPS_PER_ROW = {"dirichlet": 16, "biharmonic": 34}
 # DRAM bytes (read + write) of one k_solve_biharmonic_f<float, 1, float> launch in the 256^3 FP32
 # step, from one ncu capture of that launch (dram__bytes_read.sum + dram__bytes_write.sum)
-BIH_TRAFFIC_BYTES = 652_873_216 + 191_914_496
+BIH_TRAFFIC_BYTES = 427_636_992 + 190_156_544
 KEV_EVERY = 5
 FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (NVIDIA datasheet); the line uses the probe's measurement
 # FP32 ALU peak from the unit counts: 152 SMs x 128 FP32 lanes x 2 flops (FMA) x 2.07 GHz maximum
