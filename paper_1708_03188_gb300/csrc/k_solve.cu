@@ -830,23 +830,23 @@ __global__ void __launch_bounds__(128) k_solve_biharmonic(const void* __restrict
   }
 }
 
-// ---- factored eliminations (3-D spaces, NC = 2 or 4) -------------------------------------
-// The factorisation of one (column group, parity) system - reciprocal pivots, multipliers, the
-// reduced super-diagonals and tail coefficients - depends only on the operator (a, b, c) and on
-// kappa2, not on the right-hand side, just as the paper's Helmholtz and Biharmonic solver objects
-// are built once from their matrices and then applied to many right-hand sides (Sec. 4).
-// k_factor_* runs the top-down factorisation of the kernels above and stores it per work item in
-// a table laid out [row][value][work thread] (work thread = 32 * warp + lane of the work
-// decomposition above, so a warp reads 256 contiguous bytes per value); k_solve_*_f replays only
-// the right-hand-side recurrences from the table.  The solves run one thread per column and
-// parity (NC = 1): with no factorisation left to share between the columns of a thread, single
-// columns give four times the warps of the four-column groups, to hide the FP64 latency and to
-// share the SMs with a concurrent solve's kernels in small, even units (and a quarter of the
-// registers).  The table holds one entry per pair of columns +-l1 (k_factor_*<2>), read by both.
-// FP64 operations per row and complex column: Dirichlet 10 (against 16 with the factorisation
-// shared by a pair of columns), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal pivots are the same FP64
-// values the kernels above compute; the back substitution adds the term of the unknown just
-// solved last, so that its dependent chain is one FMA and one multiply per row.
+// ---- factored eliminations (3-D spaces) ---------------------------------------------------
+// The factorisation of one (column, parity) system - reciprocal pivots, multipliers, the reduced
+// super-diagonals and tail coefficients - depends only on the operator (a, b, c) and on kappa2,
+// not on the right-hand side, just as the paper's Helmholtz and Biharmonic solver objects are
+// built once from their matrices and then applied to many right-hand sides (Sec. 4).
+// k_factor_* runs the top-down factorisation of the kernels above, one thread per pair of columns
+// +-l1 (which share kappa2) and parity, and stores it in a table laid out [row][value][entry]
+// (entry = 32 * warp + lane of that pair decomposition, so a warp reads 256 contiguous bytes per
+// value); k_solve_*_f replays only the right-hand-side recurrences from the table, one thread per
+// column and parity (NC = 1), both columns of a pair reading the pair's entry.  With no
+// factorisation left to share between the columns of a thread, single columns give four times the
+// warps of the four-column groups, to hide the FP64 latency and to share the SMs with a concurrent
+// solve's kernels in small, even units (and a quarter of the registers).  FP64 operations per row
+// and complex column: Dirichlet 10 (against 16 with the factorisation shared by a pair of
+// columns), biharmonic 18 (against ~30 with it shared by four).  The multipliers and reciprocal
+// pivots are the same FP64 values the kernels above compute; the back substitution adds the term
+// of the unknown just solved last, so that its dependent chain is one FMA and one multiply per row.
 enum { FD_MU = 0, FD_R, FD_G, FD_GE, FD_COUNT };                        // Dirichlet table values
 enum { FB_MU = 0, FB_MU1, FB_R, FB_U1, FB_U2, FB_H0, FB_H1, FB_COUNT };  // biharmonic table values
 

@@ -5,8 +5,9 @@ A 3-D Shen-Dirichlet or Shen-biharmonic space stores the FP64 factorisation of e
 coefficients (least recently used slot replaced).  Checked here, each result against the
 oracle's dense LU per column:
   - repeated coefficients (slot hits), three alternating operators (replacement) and the mass
-    solve of the forward transform in between, on square (four-column groups for the biharmonic
-    basis) and non-square Fourier boxes, FP64 and FP32;
+    solve of the forward transform in between, on square and non-square Fourier boxes with even
+    and odd lengths along axis 1 (the table entry of a pair of columns +-l1 serves both; the
+    columns l1 = 0 and, for even lengths, l1 = -M1/2 have their own), FP64 and FP32;
   - the spectral column layout (sgm_helmholtz_solve) and the padded layout of the streaming
     physical-to-physical solve (sgm_helmholtz) alternating on one FP32 space;
   - a solve captured in a CUDA graph (inside a capture the self-contained elimination kernels
@@ -84,7 +85,8 @@ SEQUENCE = [0, 0, 1, 0, 2, 1, 0, 2, 2]
 @pytest.mark.parametrize("kinds,sizes", [(["dirichlet", "c2c", "r2c"], [24, 40, 64]),
                                          (["dirichlet", "c2c", "r2c"], [24, 16, 16]),
                                          (["biharmonic", "c2c", "r2c"], [32, 16, 16]),
-                                         (["biharmonic", "c2c", "r2c"], [32, 33, 34])],
+                                         (["biharmonic", "c2c", "r2c"], [32, 33, 34]),
+                                         (["dirichlet", "c2c", "r2c"], [20, 9, 12])],
                          ids=lambda v: "-".join(map(str, v)))
 def test_slot_hits_and_replacement(kinds, sizes, prec):
     kind = kinds[0]
